@@ -21,10 +21,12 @@
  *   - Summation order of one update (the "canonical" order; W/E, S/N, D/U
  *     are the -/+ neighbours along x, y, z):
  *         1D:    s = x_W + x_E
- *         2D/3D: s = (x_W + x_S) + (x_E + x_N);  3D only: s = s + (x_D + x_U)
+ *         2D:    s = (x_W + x_S) + (x_E + x_N)
+ *         3D:    s = ((x_W + x_D) + (x_E + x_U)) + (x_S + x_N)
  *         t = s + f_p;      x'_p = t / (2d)   (IEEE division, round to nearest)
- *     Any fixed order gives a valid Jacobi iterate; this one is fixed so that
- *     two implementations can agree bit for bit.
+ *     i.e. the x pair is interleaved with the pair along the last axis.  Any
+ *     fixed order gives a valid Jacobi iterate; this one is fixed so that two
+ *     implementations can agree bit for bit.
  *   - Residual r_p = t_p - (2d) * x_p with the same t_p; it equals
  *     (b - A x)_p where A is the grid negative Laplacian and b holds f plus
  *     the Dirichlet values of ghost neighbours.
@@ -129,8 +131,9 @@ static inline double neighbour_sum_plus_f(const grid_t* G, const double* a, int6
   if (G->ndim == 1) {
     s = a[p - G->s[0]] + a[p + G->s[0]];
   } else {
-    s = (a[p - G->s[0]] + a[p - G->s[1]]) + (a[p + G->s[0]] + a[p + G->s[1]]);
-    if (G->ndim == 3) s = s + (a[p - G->s[2]] + a[p + G->s[2]]);
+    const int64_t sl = G->s[G->ndim - 1];   /* stride of the last axis */
+    s = (a[p - G->s[0]] + a[p - sl]) + (a[p + G->s[0]] + a[p + sl]);
+    if (G->ndim == 3) s = s + (a[p - G->s[1]] + a[p + G->s[1]]);
   }
   return s + fp;
 }
@@ -335,8 +338,9 @@ static void sweep_low(const grid_t* G, const float* src, const float* r, float* 
         if (G->ndim == 1) {
           s = src[p - G->s[0]] + src[p + G->s[0]];
         } else {
-          s = (src[p - G->s[0]] + src[p - G->s[1]]) + (src[p + G->s[0]] + src[p + G->s[1]]);
-          if (G->ndim == 3) s = s + (src[p - G->s[2]] + src[p + G->s[2]]);
+          const int64_t sl = G->s[G->ndim - 1];
+          s = (src[p - G->s[0]] + src[p - sl]) + (src[p + G->s[0]] + src[p + sl]);
+          if (G->ndim == 3) s = s + (src[p - G->s[1]] + src[p + G->s[1]]);
         }
         const float t = s + r[didx(G, i, j, k)];
         const float v = t / two_d;

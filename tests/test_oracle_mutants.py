@@ -11,14 +11,16 @@ from tests import test_oracle_pins as pins
 
 MUTANTS = {
     # a dropped neighbour in the 2D/3D sum
-    "drop_north": ("(a[p + G->s[0]] + a[p + G->s[1]])", "(a[p + G->s[0]] + 0.0)"),
+    "drop_north": ("(a[p + G->s[0]] + a[p + sl])", "(a[p + G->s[0]] + 0.0)"),
     # a wrong sign on one neighbour
-    "sign_east": ("(a[p + G->s[0]] + a[p + G->s[1]])", "(-a[p + G->s[0]] + a[p + G->s[1]])"),
+    "sign_east": ("(a[p + G->s[0]] + a[p + sl])", "(-a[p + G->s[0]] + a[p + sl])"),
     # wrong divisor (d instead of 2d)
     "divisor": ("dst[p] = neighbour_sum_plus_f(G, src, p, fp) / two_d;",
                 "dst[p] = neighbour_sum_plus_f(G, src, p, fp) / (two_d - 1.0);"),
     # transposed index in the y neighbour (x stride used twice)
-    "transposed": ("s = (a[p - G->s[0]] + a[p - G->s[1]])", "s = (a[p - G->s[0]] + a[p - G->s[0]])"),
+    "transposed": ("s = (a[p - G->s[0]] + a[p - sl])", "s = (a[p - G->s[0]] + a[p - G->s[0]])"),
+    # 3D: the y pair replaced by a second z pair
+    "axis3d": ("if (G->ndim == 3) s = s + (a[p - G->s[1]] + a[p + G->s[1]]);", "if (G->ndim == 3) s = s + (a[p - G->s[2]] + a[p + G->s[2]]);"),
     # source term dropped from the update
     "no_source": ("  return s + fp;", "  return s + 0.0 * fp;"),
     # residual with the wrong sign on the diagonal term
