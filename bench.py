@@ -1,0 +1,368 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 over-decomposed Jacobi library.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload poisson2d_8192|laplace2d_256|poisson3d_512]
+
+Workload (default): 2D 5-point Poisson, 8192x8192 FP64, over-decomposed into
+16x16 blocks of 512x512 with device-side halo exchange, seeded uniform[0,1)
+boundary and initial field, source normal(0,1).  One step is the workload's
+whole run: 1000 Jacobi sweeps with the residual tested every 50 sweeps
+(jacobi_solve with an unreachable tolerance and max_sweeps = 1000).  It is
+timed for the plain FP64 path (the headline `value`) and for the FP32-inner
+and BF16-stored-inner iterative refinement with 50 inner sweeps per FP64
+outer step.  Inputs are 1.6 GB per sweep, far larger than the 129 MB L2.
+
+Under torchrun (N > 1) every rank solves its own copy of the problem (the
+solves are independent: weak scaling, no collective on the data path); the
+barrier and the max-over-ranks time only bracket the timed region.
+
+--impl reference times the CPU oracle (plain C, all host cores) on a bounded
+sample of the same workload: the paper's code is not available, so the oracle
+is the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SWEEPS_PER_STEP = 1000
+CHECK_EVERY = 50
+HBM_PEAK_FALLBACK = 6800.0
+# FP64 pipe: 1.25 TFLOP/s nominal counts an FMA as 2 flops, i.e. 0.625e12 FP64
+# instructions/s = 152 SMs x 2.07 GHz x ~2 per SM per clock.  An FP64
+# addition is one instruction, so the ALU roof for additions is 625 G/s.
+FP64_ADD_PEAK_G = 625.0
+# FP64 additions one update needs in the canonical order with pair sharing
+FP64_ADDS_PER_LUP = {2: 3.0, 3: 5.0}
+BYTES_PER_LUP = {"f64": 24.0, "f32_refine": 12.0, "bf16_refine": 8.0}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="poisson2d_8192",
+                    choices=["poisson2d_8192", "laplace2d_256", "poisson3d_512"])
+    ap.add_argument("--forms", default="f64,f32_refine,bf16_refine")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return HBM_PEAK_FALLBACK, "fallback"
+
+
+def make_workload(name):
+    from paper_2303_02543_gb300 import inputs
+    if name == "poisson2d_8192":
+        p = inputs.poisson_2d_large()
+        desc = "2D 5-point Poisson 8192x8192 FP64, 16x16 blocks of 512x512, 1000 sweeps, residual every 50"
+    elif name == "laplace2d_256":
+        p = inputs.laplace_2d_small()
+        desc = "2D 5-point Laplace 256x256 FP64, 4x4 blocks of 64x64, 100 sweeps"
+    else:
+        p = inputs.poisson_3d()
+        desc = "3D 7-point Poisson 512^3 FP64, blocks of 64^3, sweeps with residual every 50"
+    sweeps = 100 if name == "laplace2d_256" else SWEEPS_PER_STEP
+    return p, desc, sweeps
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---- CPU oracle timing ------------------------------------------------------
+
+def oracle_sample(p, sweeps):
+    """Time the oracle (all host cores) on `sweeps` sweeps of the workload with
+    residual tests at both ends; returns (GLUP/s, seconds, threads)."""
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    oracle.solve(p.dims, p.faces, p.source, p.x0, 1e-300, sweeps, CHECK_EVERY)
+    dt = time.perf_counter() - t0
+    return p.points * sweeps / dt / 1e9, dt, oracle.max_threads()
+
+
+def cpu_baseline(p, name):
+    sweeps = {"poisson2d_8192": 50, "laplace2d_256": 2000, "poisson3d_512": 20}[name]
+    glups, dt, cores = oracle_sample(p, sweeps)
+    return {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
+            "sample": f"{sweeps} sweeps of the full {'x'.join(map(str, p.dims))} grid with residual tests "
+                      f"before and after ({dt:.1f} s, OpenMP on {cores} threads)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    p, desc, _ = make_workload(args.workload)
+    sweeps = {"poisson2d_8192": 5, "laplace2d_256": 500, "poisson3d_512": 2}[args.workload]
+    for _ in range(args.warmup):
+        oracle_sample(p, sweeps)
+    t0 = time.perf_counter()
+    cores = 1
+    for _ in range(args.steps):
+        _, _, cores = oracle_sample(p, sweeps)
+    dt = time.perf_counter() - t0
+    glups = p.points * sweeps * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": "Jacobi GLUP/s (FP64 plain)", "value": glups, "unit": "GLUP/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "description": desc,
+                       "sample": f"{sweeps} sweeps per step (bounded sample of the {SWEEPS_PER_STEP}-sweep run)"},
+            "cpu_baseline": {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{sweeps} sweeps per step x {args.steps} steps"},
+            "e2e": {"value": glups, "unit": "GLUP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---- GPU arm ----------------------------------------------------------------
+
+def time_form(p, form, sweeps, args, world, stream, sampler=None):
+    import torch
+    from paper_2303_02543_gb300 import jacobi as J
+    s = J.Solver(p.dims, p.block, dtype=form, faces=p.faces, source=p.source, x0=p.x0,
+                 check_every=CHECK_EVERY, refine_period=CHECK_EVERY, profile=1)
+
+    def step():
+        st, sw, rel = s.solve(1e-300, sweeps)
+        if st not in (J.OK, J.ERR_NOT_CONVERGED) or sw != sweeps:
+            raise RuntimeError(f"step failed: status {st}, sweeps {sw}")
+        return rel
+
+    for _ in range(args.warmup):
+        step()
+    kern = "sweep_f64" if form == "f64" else "sweep_low"
+    for k in ("sweep_f64", "sweep_low", "refine_outer", "reduce", "halo"):
+        s.profile(k, reset=True)
+    launches0 = s.profile("all")[1]
+    barrier(world)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        rel = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop() if sampler else None
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    kms, kn = s.profile(kern)
+    launches = s.profile("all")[1] - launches0
+    other = {k: s.profile(k) for k in ("refine_outer", "reduce", "halo")}
+    out = {"ms": ms, "kernel": kern, "kernel_ms": kms, "kernel_launches": kn, "launches": launches,
+           "rel": rel, "clocks": clocks, "other": other, "solver": s}
+    return out
+
+
+def e2e_form(s, p, sweeps, args, world, stream):
+    """Same step through the C ABI with host buffers: upload x from pinned host
+    memory, run the step, read the field back into pinned host memory."""
+    import torch
+    x_host = torch.from_numpy(p.x0.copy()).pin_memory()
+    out = torch.empty(p.shape, dtype=torch.float64).pin_memory()
+    for _ in range(max(1, args.warmup - 2)):
+        s.set_field(x_host)
+        s.solve(1e-300, sweeps)
+        s.field(out)
+    barrier(world)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        s.set_field(x_host)
+        st, sw, rel = s.solve(1e-300, sweeps)
+        s.field(out)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    nbytes = p.points * 8
+    return ms, nbytes, nbytes + 16
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2303_02543_gb300 import build as B
+    if rank == 0 and not B.up_to_date():
+        B.build()
+    barrier(world)
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    p, desc, sweeps = make_workload(args.workload)
+    hbm_peak, peak_kind = measured_peaks()
+    forms = [f for f in args.forms.split(",") if f]
+    results = {}
+    clocks = None
+    head = forms[0]
+    for form in forms:
+        sampler = ClockSampler(torch.cuda.current_device()) if form == head and rank == 0 else None
+        results[form] = time_form(p, form, sweeps, args, world, stream, sampler)
+        if sampler:
+            clocks = results[form]["clocks"]
+    h = results[head]
+    lups = p.points * sweeps * args.steps * world
+    value = lups / (h["ms"] / 1e3) / 1e9
+    e2e = None
+    if not args.no_e2e:
+        ms_e2e, h2d, d2h = e2e_form(h["solver"], p, sweeps, args, world, stream)
+        e2e = {"value": lups / (ms_e2e / 1e3) / 1e9, "unit": "GLUP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+    # roofline of the dominant kernel of the headline form
+    nd = p.ndim
+    per_launch_ms = h["kernel_ms"] / max(1, h["kernel_launches"])
+    lup_rate = p.points / (per_launch_ms / 1e3)
+    if head == "f64":
+        achieved = FP64_ADDS_PER_LUP[nd] * lup_rate / 1e9
+        roof = {"bound": "alu", "kernel": "sweep_f64", "achieved": achieved, "peak": FP64_ADD_PEAK_G,
+                "unit": "GFLOP/s", "frac": achieved / FP64_ADD_PEAK_G, "traffic": None,
+                "peak_kind": "derived: 1.25 TFLOP/s FP64 nominal = 625 G FP64 instructions/s (adds)",
+                "hbm": {"achieved": BYTES_PER_LUP[head] * lup_rate / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": BYTES_PER_LUP[head] * lup_rate / 1e9 / hbm_peak, "peak_kind": peak_kind,
+                        "bytes_per_lup": BYTES_PER_LUP[head]}}
+    else:
+        achieved = BYTES_PER_LUP[head] * lup_rate / 1e9
+        roof = {"bound": "hbm", "kernel": "sweep_low", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind}
+    forms_out = {}
+    for form, r in results.items():
+        kl = r["kernel_ms"] / max(1, r["kernel_launches"])
+        lr = p.points / (kl / 1e3)
+        forms_out[form] = {
+            "glups": p.points * sweeps * args.steps * world / (r["ms"] / 1e3) / 1e9,
+            "ms_per_step": r["ms"] / args.steps,
+            "kernel": r["kernel"], "kernel_us": kl * 1e3,
+            "kernel_hbm_gbs": BYTES_PER_LUP[form] * lr / 1e9,
+            "kernel_hbm_frac": BYTES_PER_LUP[form] * lr / 1e9 / hbm_peak,
+            "rel_residual_after": r["rel"],
+            "launches_per_step": r["launches"] / args.steps,
+            "other_kernels_ms": {k: v[0] / args.steps for k, v in r["other"].items()},
+        }
+        r["solver"].close()
+    line = {
+        "metric": "Jacobi GLUP/s (FP64 plain; mixed forms in `forms`)",
+        "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": h["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if head == "f64" else head, "data": "synthetic",
+        "config": {"workload": args.workload, "description": desc, "grid": list(p.dims),
+                   "block": list(p.block), "sweeps_per_step": sweeps, "check_every": CHECK_EVERY,
+                   "refine_period": CHECK_EVERY,
+                   "l2": "inputs larger than L2 (no flush)" if p.points * 24 > 129e6 else "L2-resident",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": roof, "forms": forms_out, "clocks": clocks, "e2e": e2e,
+        "gpu_launches": int(h["launches"]),
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(p, args.workload)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

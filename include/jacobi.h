@@ -1,0 +1,172 @@
+/*
+ * jacobi.h -- C ABI of the GB300 over-decomposed Jacobi library.
+ *
+ * The operation is the Jacobi relaxation of the paper's Jacobi3D proxy
+ * application (section 4.3: a fixed number of Jacobi iterations on a 3D
+ * domain decomposed into cuboids; every iteration packs the faces of each
+ * cuboid, moves them to the neighbours, unpacks them into the halos and then
+ * applies the update) with the over-decomposition of section 4.4 (more blocks
+ * than processors).  The paper never writes the equation down; this library
+ * solves the Poisson problem -Lap(u) = f with Dirichlet values g on a grid of
+ * unit spacing with the 5-point (2D) or 7-point (3D) stencil, iterating
+ *
+ *     x'_p = (sum of the 2d neighbours of p + f_p) / (2d)
+ *
+ * with the fixed summation order ((W+S)+(E+N))+f in 2D and
+ * (((W+D)+(E+U))+(S+N))+f in 3D (W/E, S/N, D/U = -/+ neighbour along x, y, z).
+ * The residual is r = b - A x with A the grid negative Laplacian and b = f plus
+ * the Dirichlet values of boundary neighbours; the relative residual is
+ * ||r||_2 / ||b||_2 (||r||_2 when b = 0).
+ *
+ * Array conventions (all arguments):
+ *   - Fields (x, f) are "interior-dense": nz*ny*nx doubles (2D: ny*nx), x
+ *     fastest, no ghost points.
+ *   - Boundary faces are ordered -x,+x,-y,+y,-z,+z.  A face lists its points
+ *     with the two other axes in order, lowest axis fastest: an x face has
+ *     ny*nz values (y fastest), a y face nx*nz (x fastest), a z face nx*ny.
+ *     In 2D the x faces have ny values and the y faces nx values.
+ *   - Host pointers are copied before the call returns; the caller keeps
+ *     ownership.  Device pointers (on_device = 1) must be device memory of the
+ *     current device, readable/writable on the library's stream.
+ *   - All device state belongs to the library and is released by the destroy
+ *     call.  Device memory comes from the allocator registered with
+ *     jacobi_set_allocator (cudaMalloc when none).
+ *
+ * Errors: every call returns a jacobi_status; no C++ exception crosses this
+ * boundary and nothing aborts.  jacobi_last_error(ctx) returns a message for
+ * the last failure of ctx (or of the calling thread when ctx is NULL).  After
+ * JACOBI_ERR_CUDA the context should be destroyed.
+ *
+ * Threads: one context must not be used by two threads at the same time.
+ * Distinct contexts are independent.
+ */
+#ifndef JACOBI_GB300_H
+#define JACOBI_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  JACOBI_OK = 0,
+  JACOBI_ERR_INVALID = 1,        /* bad argument or option */
+  JACOBI_ERR_OOM = 2,            /* device allocation failed */
+  JACOBI_ERR_CUDA = 3,           /* a CUDA call failed */
+  JACOBI_ERR_NOT_CONVERGED = 4,  /* solve stopped at max_sweeps above tol */
+  JACOBI_ERR_DIVERGED = 5,       /* residual became NaN or infinite */
+  JACOBI_ERR_TIMEOUT = 6,        /* a bounded device-side wait ran out */
+  JACOBI_ERR_BUSY = 7            /* server: request pending or cannot be admitted */
+} jacobi_status;
+
+/* Arithmetic of the iteration.
+ *   JACOBI_F64          plain FP64 Jacobi sweeps.
+ *   JACOBI_F32_REFINE   iterative refinement: r = b - A x and x += e in FP64,
+ *                       inner Jacobi sweeps of A e = r (zero boundary) in FP32.
+ *   JACOBI_BF16_REFINE  as F32_REFINE with e stored as bfloat16 (RNE) and the
+ *                       inner sweeps computed in FP32; r stored as FP32 (or
+ *                       bfloat16 with option "r_bf16" = 1). */
+typedef enum { JACOBI_F64 = 0, JACOBI_F32_REFINE = 1, JACOBI_BF16_REFINE = 2 } jacobi_dtype;
+
+typedef enum { JACOBI_BC_ZERO = 0, JACOBI_BC_CONST = 1, JACOBI_BC_FACES = 2 } jacobi_bc_kind;
+
+/* Dirichlet boundary: zero, one constant `value`, or per-face host arrays
+ * (faces[i] may be NULL for a zero face). */
+typedef struct {
+  int kind;               /* jacobi_bc_kind */
+  double value;           /* JACOBI_BC_CONST */
+  const double* faces[6]; /* JACOBI_BC_FACES, host memory */
+} jacobi_boundary;
+
+typedef struct jacobi_ctx* jacobi_t;
+
+/* Allocator hooks: alloc(bytes, cuda_stream, user) returns device memory or
+ * NULL; free(ptr, cuda_stream, user).  Pass NULLs to restore cudaMalloc.
+ * Affects contexts created afterwards. */
+void jacobi_set_allocator(void* (*alloc)(size_t, void*, void*), void (*free_fn)(void*, void*, void*), void* user);
+
+/* Create a solver for one grid (section 4.3's decomposed domain).
+ *   ndim      2 or 3.
+ *   dims      interior points {nx, ny, nz} (nz ignored in 2D), each >= 1.
+ *   block     block extent per axis (section 4.4's over-decomposition),
+ *             1 <= block[a] <= dims[a]; blocks that do not divide a dimension
+ *             leave a smaller remainder block at the high end.  block = dims
+ *             gives the monolithic (single-block) solver.
+ *   dtype     jacobi_dtype.
+ *   bc        boundary (NULL: zero).
+ *   source    host f, interior-dense (NULL: f = 0).
+ *   x0        host initial iterate, interior-dense (NULL: 0).
+ *   cuda_stream  cudaStream_t all work is issued on (NULL: the legacy default
+ *             stream).
+ * On success *out holds the context; on failure *out is NULL. */
+jacobi_status jacobi_create(jacobi_t* out, int ndim, const int64_t dims[3], const int64_t block[3],
+                            int dtype, const jacobi_boundary* bc, const double* source, const double* x0,
+                            void* cuda_stream);
+
+/* Run n Jacobi sweeps (section 4.3's fixed-iteration loop), halo exchange
+ * included.  In the refinement dtypes: n inner sweeps in outer steps of
+ * "refine_period" sweeps, each closed by x += e.  Asynchronous. */
+jacobi_status jacobi_sweep(jacobi_t ctx, int64_t n);
+
+/* FP64 residual of the current iterate: *rel = ||b - A x|| / ||b|| (or
+ * ||b - A x|| if b = 0), *abs = ||b - A x||.  Either pointer may be NULL.
+ * Synchronises the stream. */
+jacobi_status jacobi_residual(jacobi_t ctx, double* rel, double* abs);
+
+/* Sweep until the relative residual is <= tol, testing at sweep counts 0,
+ * c, 2c, ... (c = option "check_every"; in refinement dtypes every outer step
+ * of "refine_period" inner sweeps), at most max_sweeps sweeps.  Returns
+ * JACOBI_OK, JACOBI_ERR_NOT_CONVERGED (the field is still valid) or
+ * JACOBI_ERR_DIVERGED.  *sweeps_done / *final_rel may be NULL. */
+jacobi_status jacobi_solve(jacobi_t ctx, double tol, int64_t max_sweeps, int64_t* sweeps_done,
+                           double* final_rel);
+
+/* Copy the current iterate out (interior-dense) to host (on_device = 0) or
+ * device memory.  Synchronises the stream for host output. */
+jacobi_status jacobi_get_field(jacobi_t ctx, double* out, int on_device);
+
+/* Replace the current iterate (interior-dense, host or device memory). */
+jacobi_status jacobi_set_field(jacobi_t ctx, const double* in, int on_device);
+
+/* Replace the source term f (interior-dense, host or device memory). */
+jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
+
+/* Integer options:
+ *   "check_every"    sweeps between residual tests in jacobi_solve (F64), >= 1
+ *   "refine_period"  inner sweeps per outer refinement step, >= 1
+ *   "halo"           0 = fused into the sweep (default), 1 = separate pack/unpack kernels
+ *   "rows_f64"       lines per warp work item of the FP64 kernels (>= 1)
+ *   "rows_low"       lines per warp work item of the low-precision kernels (>= 1)
+ *   "r_bf16"         BF16_REFINE only: store r as bfloat16 (0/1)
+ *   "profile"        1: time every kernel launch with CUDA events (see jacobi_profile) */
+jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value);
+jacobi_status jacobi_get_option(jacobi_t ctx, const char* key, int64_t* value);
+
+/* Kernel timing collected while option "profile" = 1: total milliseconds and
+ * number of launches of the kernel class `kernel` ("sweep_f64", "sweep_low",
+ * "refine_outer", "reduce", "halo").  Synchronises the stream.  reset = 1
+ * clears the counters afterwards.  kernel = "all" reports, in *launches, every
+ * kernel launch the context has issued since creation (profiling not needed)
+ * and 0 in *total_ms. */
+jacobi_status jacobi_profile(jacobi_t ctx, const char* kernel, double* total_ms, int64_t* launches, int reset);
+
+/* Bytes of device memory held by the context. */
+jacobi_status jacobi_device_bytes(jacobi_t ctx, int64_t* bytes);
+
+/* NULL-safe. */
+void jacobi_destroy(jacobi_t ctx);
+
+/* Message of the last failure of ctx (thread-local message when ctx is NULL).
+ * The string stays valid until the next call on the same context/thread. */
+const char* jacobi_last_error(jacobi_t ctx);
+
+/* Library version: major * 10000 + minor * 100 + patch. */
+int jacobi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* JACOBI_GB300_H */

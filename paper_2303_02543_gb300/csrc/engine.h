@@ -1,0 +1,195 @@
+// Host-side engine: a "workset" is a set of independent Jacobi solves whose
+// blocks are processed together by every kernel launch.  A single-grid
+// context is a workset of one solve; the batch and server interfaces add and
+// retire solves.  Over-decomposition (section 4.4) is the block table: every
+// block of every solve becomes warp work items in one table, so one launch
+// covers all blocks and all solves.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "jacobi_internal.h"
+
+namespace jgb {
+
+struct JErr {
+  int code;
+  std::string msg;
+};
+
+struct AllocHooks {
+  void* (*alloc)(size_t, void*, void*) = nullptr;
+  void (*free)(void*, void*, void*) = nullptr;
+  void* user = nullptr;
+};
+
+AllocHooks current_alloc_hooks();
+void set_alloc_hooks(const AllocHooks& h);
+
+// Owns device allocations made through the hooks captured at construction.
+class DevPool {
+ public:
+  DevPool(const AllocHooks& h, cudaStream_t s) : hooks_(h), stream_(s) {}
+  ~DevPool();
+  void* alloc(size_t bytes);        // zero bytes -> nullptr; failure throws JErr(OOM)
+  void release(void* p);            // frees one allocation
+  int64_t bytes() const { return bytes_; }
+
+ private:
+  struct Rec {
+    void* p;
+    size_t n;
+  };
+  AllocHooks hooks_;
+  cudaStream_t stream_;
+  std::vector<Rec> recs_;
+  int64_t bytes_ = 0;
+};
+
+// Problem description of one solve (host memory).
+struct ProblemSpec {
+  int ndim = 2;
+  int64_t n[3] = {1, 1, 1};
+  int64_t blk[3] = {1, 1, 1};
+  int bc_kind = 0;
+  double bc_value = 0.0;
+  const double* faces[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  const double* source = nullptr;
+  const double* x0 = nullptr;
+  int inputs_on_device = 0;
+};
+
+struct SolveHost {
+  ProblemSpec spec;
+  int nb[3] = {1, 1, 1};
+  int slot = -1;                 // index in the solve table
+  int64_t elems = 0;             // elements per array in the layout
+  int64_t face_elems = 0;        // elements of the face send buffers
+  int64_t nparts = 0;
+  int part_row = 0;
+  int nchunks = 0;
+  double bss = 0.0;              // ||b||^2
+  std::vector<BlockDev> blocks;  // nbr indices are local (0-based within the solve)
+  // device memory (owned by the workset pool)
+  double* x[2] = {nullptr, nullptr};
+  double* f = nullptr;
+  void* e[2] = {nullptr, nullptr};
+  void* r = nullptr;
+  double* send64 = nullptr;
+  void* sendlo = nullptr;
+  double* part = nullptr;
+  double* lvl1 = nullptr;
+  std::vector<void*> allocs;
+  // host mirrors of device state
+  int phase = 0;
+  int apply_e = 0;
+  int active = 1;
+  int64_t points() const { return spec.n[0] * spec.n[1] * spec.n[2]; }
+};
+
+enum ProfKind { kProfSweepF64 = 0, kProfSweepLow, kProfOuter, kProfReduce, kProfHalo, kProfCount };
+
+struct Options {
+  int64_t check_every = 50;
+  int64_t refine_period = 20;
+  int64_t halo = 0;          // 0 fused, 1 standalone pack/unpack
+  int64_t rows_f64 = 32;
+  int64_t rows_low = 32;
+  int64_t r_bf16 = 0;
+  int64_t profile = 0;
+};
+
+class Workset {
+ public:
+  Workset(int ndim, int dtype, cudaStream_t stream, int capacity);
+  ~Workset();
+
+  // Adds a solve, uploads its inputs, computes ||b||; returns its slot.
+  int add_solve(const ProblemSpec& p);
+  void remove_solve(int slot);
+  void rebuild_tables();
+
+  // Plain FP64 sweeps of every active solve; with resid_last the last sweep
+  // also reduces the residual of its input iterate.
+  void sweeps_f64(int64_t n, bool resid_last);
+  void phase_advance(int d, int set_apply_e);
+  // Residual of the current iterate of every active solve (no sweep).
+  void residual_only();
+  // Refinement: outer step (x += e if pending; r; reduction), then k inner sweeps.
+  void refine_outer();
+  void refine_inner(int64_t k);
+  // Read the sums of squares of every slot (synchronises).
+  void read_rss(std::vector<double>& out);
+  void set_active(int slot, int active);
+  void sync();
+
+  void scatter(int slot, const double* dense, int which, int on_device);
+  void gather(int slot, double* dense, int on_device);
+  void halo_exchange_x(int kpar);
+
+  // profiling
+  void prof_begin(int kind);
+  void prof_end(int kind);
+  void prof_collect(int kind, double* ms, int64_t* n, bool reset);
+
+  bool refine() const { return dtype_ != 0; }
+  int ndim() const { return ndim_; }
+  int dtype() const { return dtype_; }
+  int low() const { return dtype_ == 2 ? kLowBF16 : kLowF32; }
+  cudaStream_t stream() const { return stream_; }
+  SolveHost* solve(int slot) { return slot >= 0 && slot < (int)solves_.size() ? solves_[slot] : nullptr; }
+  int capacity() const { return capacity_; }
+  int64_t device_bytes() const { return pool_.bytes(); }
+  int last_epar() const { return epar_last_; }
+  int64_t launches() const { return launches_; }
+
+  Options opt;
+
+ private:
+  void layout_solve(SolveHost& s);
+  void alloc_solve(SolveHost& s);
+  void upload_inputs(SolveHost& s);
+  void push_solve_dev(SolveHost& s);
+  Tables tables() const;
+  Tables solve_tables(const SolveHost& s) const;
+  void reduce();
+
+  int ndim_, dtype_, capacity_;
+  cudaStream_t stream_;
+  DevPool pool_;
+  std::vector<SolveHost*> solves_;   // slot -> solve (nullptr when free)
+  // device tables
+  SolveDev* d_solves_ = nullptr;
+  double* d_rss_ = nullptr;
+  uint32_t* d_ticket_ = nullptr;
+  double* h_rss_ = nullptr;          // pinned
+  BlockDev* d_blocks_ = nullptr;
+  WorkItem* d_w64_ = nullptr;
+  WorkItem* d_wlo_ = nullptr;
+  FaceItem* d_faces_ = nullptr;
+  RedItem* d_red_ = nullptr;
+  RowItem* d_rows_ = nullptr;
+  int n64_ = 0, nlo_ = 0, nfaces_ = 0, nred_ = 0, nrows_ = 0;
+  std::vector<void*> table_allocs_;
+  std::vector<int> block_base_;      // slot -> first block index in the table
+  std::vector<int> face_base_, face_cnt_, row_base_, row_cnt_;
+  int epar_last_ = 0;
+  int64_t launches_ = 0;           // kernel launches issued so far
+  bool tables_dirty_ = true;
+  // profiling events
+  struct EvPair {
+    cudaEvent_t a, b;
+  };
+  std::vector<EvPair> ev_pending_[kProfCount];
+  std::vector<cudaEvent_t> ev_free_;
+  double prof_ms_[kProfCount] = {0, 0, 0, 0, 0};
+  int64_t prof_n_[kProfCount] = {0, 0, 0, 0, 0};
+  cudaEvent_t ev_open_ = nullptr;
+};
+
+}  // namespace jgb

@@ -1,0 +1,133 @@
+// Internal data structures shared by the host engine and the CUDA kernels.
+//
+// Layout of one solve in HBM (the over-decomposed domain of section 4.4: the
+// grid is cut into blocks, each block a task with its own storage):
+//
+//   * Every array of a solve (x[0], x[1], f in FP64; e[0], e[1], r in the
+//     low-precision type) uses the SAME element layout, so one element offset
+//     addresses a point in all of them.
+//   * Block main array: planes z = -gz .. bz-1+gz (gz = 1 in 3D, 0 in 2D),
+//     rows y = -1 .. by, each row `pitch` elements holding x = 0 .. bx-1.
+//     Rows -1 and by (and planes -1 and bz in 3D) are the ghost ring along
+//     y (and z); element (x, y, z) sits at off + (z+gz)*plane + (y+1)*pitch + x.
+//     pitch is a multiple of 16 elements and off a multiple of 32, so rows are
+//     128-byte aligned for FP64 and 64-byte aligned for FP32.
+//   * The ghost ring along x is stored apart, as two contiguous columns
+//     (gW then gE, bz*by elements each, y fastest) at xoff, so that reading a
+//     block's west/east ghosts costs a contiguous stream, not one sector per
+//     row.
+//   * Ghosts on the domain boundary hold the Dirichlet values g (x) or 0 (e)
+//     and are written once; ghosts on block boundaries are rewritten after
+//     every sweep by the halo exchange (section 4.3: pack, transfer, unpack).
+#pragma once
+#include <stdint.h>
+
+namespace jgb {
+
+constexpr int kWarps = 8;            // warps per CTA of the sweep kernels
+constexpr int kThreads = 32 * kWarps;
+constexpr int kSegF64 = 64;          // points per warp row, FP64 kernels (2 per lane)
+constexpr int kSegLow = 128;         // points per warp row, low-precision kernels (4 per lane)
+constexpr int kResSeg = 64;          // points per residual partial (fixed: decomposition independent)
+constexpr int kRedThreads = 256;     // threads of the reduction kernel
+constexpr int kRedChunk = 4096;      // partials summed by one reduction CTA
+
+enum LowType { kLowF32 = 0, kLowBF16 = 1 };
+
+// Neighbour order: -x, +x, -y, +y, -z, +z.
+struct BlockDev {
+  int64_t off;        // element offset of the main array (plane -gz, row -1)
+  int64_t xoff;       // element offset of the x ghost columns
+  int64_t part;       // first residual slot of this block column (solve-relative)
+  int64_t foff;       // element offset of this block's 6 face send buffers (standalone halo)
+  int32_t bx, by, bz;
+  int32_t pitch;      // elements per row
+  int32_t plane;      // elements per plane = (by + 2) * pitch
+  int32_t gz;         // 1 in 3D, 0 in 2D
+  int32_t oy, oz;     // origin of the block in the solve grid (y, z)
+  int32_t solve;      // index into the solve table
+  int32_t nbr[6];     // neighbour block index (table-wide) or -1 on the domain boundary
+  int32_t fsz[6];     // elements of each face send buffer
+  int32_t ox;         // origin of the block in the solve grid (x)
+};
+
+struct SolveDev {
+  double* x[2];       // FP64 iterate, ping-pong
+  double* f;          // FP64 source (interior points only are read)
+  void* e[2];         // low-precision correction, ping-pong
+  void* r;            // low-precision residual
+  double* send64;     // face send buffers (FP64 arrays)
+  void* sendlo;       // face send buffers (low arrays)
+  double* part;       // residual partials
+  double* lvl1;       // first-level reduction results
+  double* rss;        // [0] = sum of squares written by the reduction
+  uint32_t* ticket;   // reduction ticket
+  int64_t nparts;     // residual partial slots
+  int32_t part_row;   // partial slots per grid row
+  int32_t ny;         // grid rows along y (for the partial row index)
+  int32_t ndim;
+  int32_t phase;      // x[phase] holds the current iterate
+  int32_t active;     // 0: every kernel skips this solve
+  int32_t apply_e;    // refinement: 1 once a correction e exists
+  int32_t low;        // LowType of e and r
+  int32_t r_bf16;     // 1: r stored as bfloat16 (else FP32)
+};
+
+// One warp's work: `n` consecutive rows (2D: along y) or planes (3D: along z)
+// of one segment of one block.  In 3D the row y is fixed.
+struct WorkItem {
+  int32_t block;
+  int16_t seg;
+  int16_t n;
+  int32_t y0;
+  int32_t z0;
+};
+
+// One face of one block for the standalone pack / unpack kernels.
+struct FaceItem {
+  int32_t block;
+  int32_t face;
+};
+
+// One CTA of the reduction: `len` partials of solve `solve` from `start`.
+struct RedItem {
+  int32_t solve;
+  int32_t chunk;      // chunk index within the solve
+  int32_t nchunks;    // chunks of this solve
+  int32_t len;
+  int64_t start;
+};
+
+// One CTA-row job of the dense <-> blocked copies: one row of one block.
+struct RowItem {
+  int32_t block;
+  int32_t y;
+  int32_t z;
+  int32_t pad;
+};
+
+// Kernel launch wrappers (kernels.cu).  All return cudaError_t as int.
+struct Tables {
+  const WorkItem* w64;  int n64;     // FP64 sweep / residual / refine-outer items
+  const WorkItem* wlo;  int nlo;     // low-precision sweep items
+  const FaceItem* faces; int nfaces; // interior faces
+  const RedItem* red;   int nred;    // reduction CTAs
+  const RowItem* rows;  int nrows;   // block rows
+  const BlockDev* blocks;
+  SolveDev* solves;
+  int ndim;
+};
+
+int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, void* stream);
+int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, void* stream);
+int launch_refine_outer(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream);
+int launch_halo_pack(const Tables& t, int which, int par, int low, void* stream);
+int launch_halo_unpack(const Tables& t, int which, int par, int low, void* stream);
+int launch_reduce(const Tables& t, void* stream);
+int launch_scatter(const Tables& t, const double* dense, int which, int par, int64_t nx, int64_t ny, void* stream);
+int launch_gather(const Tables& t, double* dense, int par, int64_t nx, int64_t ny, void* stream);
+int launch_ghost_fill(const Tables& t, const double* const* faces_dev, int par, int64_t nx, int64_t ny,
+                      int64_t nz, void* stream);
+int launch_phase_advance(SolveDev* solves, int nsolves, int dphase, int set_apply_e, void* stream);
+
+}  // namespace jgb

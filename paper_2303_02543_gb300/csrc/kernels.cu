@@ -1,0 +1,860 @@
+// CUDA kernels (sm_103a) for the over-decomposed Jacobi relaxation.
+//
+// Section 4.3 describes each iteration of the Jacobi3D proxy as: pack the
+// faces of every cuboid, move them to the neighbours, unpack them into the
+// halos, then run the Jacobi update once all halos are in.  Section 4.4 cuts
+// the domain into more pieces than processors.  Here every block of the
+// decomposition is a task that warps pick from a work table; the update and
+// the halo exchange are fused (each block writes its boundary layer straight
+// into its neighbours' ghost cells of the destination buffer) or run as
+// separate pack / unpack kernels.  Both give bit-identical fields.
+//
+// Canonical arithmetic of one update (W/E, S/N, D/U = -/+ neighbours along
+// x, y, z; every operation one IEEE round-to-nearest-even, no contraction):
+//   2D: t = ((W + S) + (E + N)) + f,            x' = t / 4
+//   3D: t = (((W + D) + (E + U)) + (S + N)) + f, x' = t / 6
+//   residual r = t - (2d) x, reduced as sum r^2.
+// The pair (E + N) of a point is the pair (W + S) of its diagonal neighbour
+// one row up and one column right (2D; in 3D the same holds along x and z),
+// so a warp marching along the last axis forms each such pair once and
+// passes it on: 3.5 FP64 additions per 2D update instead of 4.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "exact_f64.cuh"
+#include "jacobi_internal.h"
+
+namespace jgb {
+
+#define FULL_MASK 0xffffffffu
+
+// ---------------------------------------------------------------------------
+// scalar helpers
+
+__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+
+// t / 4, exact: exponent decrement on the integer pipe, FP64 multiply only when
+// some lane of the warp needs it (zero, subnormal, inf/NaN).
+__device__ __forceinline__ double div_2d(double t) {
+  const uint64_t b = f64_bits(t);
+  const bool fast = quarter_fast(b);
+  double q = quarter_bits(b);
+  if (!__all_sync(FULL_MASK, fast)) {
+    if (!fast) q = __dmul_rn(t, 0.25);
+  }
+  return q;
+}
+
+// t / 6, correctly rounded, integer pipe (see exact_f64.cuh); IEEE division
+// only when some lane of the warp leaves the fast range.
+__device__ __forceinline__ double div_3d(double t) {
+  const uint64_t b = f64_bits(t);
+  const bool fast = sixth_fast(b);
+  double q = sixth_bits(b);
+  if (!__all_sync(FULL_MASK, fast)) {
+    if (!fast) q = __ddiv_rn(t, 6.0);
+  }
+  return q;
+}
+
+template <int DIM>
+__device__ __forceinline__ double jdiv(double t) {
+  if constexpr (DIM == 2) return div_2d(t);
+  else return div_3d(t);
+}
+
+template <int DIM>
+__device__ __forceinline__ float jdivf(float t) {
+  if constexpr (DIM == 2) return __fmul_rn(t, 0.25f);
+  else return __fdiv_rn(t, 6.0f);
+}
+
+// low-precision element access ------------------------------------------------
+
+struct bf16x4 {
+  __nv_bfloat162 a, b;
+};
+
+__device__ __forceinline__ float to_f(float v) { return v; }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+
+template <typename T>
+__device__ __forceinline__ T from_f(float v);
+template <>
+__device__ __forceinline__ float from_f<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 from_f<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+
+// 4 consecutive elements (16-byte aligned for float, 8-byte for bf16)
+__device__ __forceinline__ float4 ld4(const float* p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float4 ld4(const __nv_bfloat16* p) {
+  const uint2 u = __ldg(reinterpret_cast<const uint2*>(p));
+  bf16x4 v;
+  memcpy(&v, &u, 8);
+  const float2 lo = __bfloat1622float2(v.a), hi = __bfloat1622float2(v.b);
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
+__device__ __forceinline__ void st4(float* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
+__device__ __forceinline__ void st4(__nv_bfloat16* p, float4 v) {
+  bf16x4 o;
+  o.a = __floats2bfloat162_rn(v.x, v.y);
+  o.b = __floats2bfloat162_rn(v.z, v.w);
+  uint2 u;
+  memcpy(&u, &o, 8);
+  *reinterpret_cast<uint2*>(p) = u;
+}
+
+__device__ __forceinline__ float comp(const float4& v, int k) {
+  return k == 0 ? v.x : k == 1 ? v.y : k == 2 ? v.z : v.w;
+}
+
+// Store the valid leading elements of a 4-vector (all 4 in one store when valid).
+template <typename T>
+__device__ __forceinline__ void st4_valid(T* p, float4 v, int nvalid) {
+  if (nvalid >= 4) {
+    st4(p, v);
+  } else {
+    if (nvalid > 0) p[0] = from_f<T>(v.x);
+    if (nvalid > 1) p[1] = from_f<T>(v.y);
+    if (nvalid > 2) p[2] = from_f<T>(v.z);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Geometry of one warp item.  The warp marches along the last axis (y in 2D,
+// z in 3D); in 3D the row y is fixed.  "Line m" is the row of the warp at
+// march index m (m = -1 and m = extent are ghost lines).
+
+template <int DIM>
+struct Geo {
+  int64_t base;   // element offset of the line at march index 0 minus one line step
+  int64_t step;   // elements between consecutive lines along the march
+  int64_t side;   // 3D: elements from a line to the same x on row y+1 (= pitch)
+  int extent;     // interior extent along the march axis
+  int col_stride; // x-ghost column index = m * col_stride + col_off
+  int col_off;
+
+  __device__ __forceinline__ Geo(const BlockDev& B, int y) {
+    if constexpr (DIM == 2) {
+      step = B.pitch;
+      base = B.off;
+      side = 0;
+      extent = B.by;
+      col_stride = 1;
+      col_off = 0;
+    } else {
+      step = B.plane;
+      base = B.off + (int64_t)(y + 1) * B.pitch;
+      side = B.pitch;
+      extent = B.bz;
+      col_stride = B.by;
+      col_off = y;
+    }
+  }
+  // offset of x = 0 on line m
+  __device__ __forceinline__ int64_t line(int m) const { return base + (int64_t)(m + 1) * step; }
+  __device__ __forceinline__ int col(int m) const { return m * col_stride + col_off; }
+};
+
+// Ghost targets of the halo push for one warp item (destination buffer).
+struct PushTargets {
+  int64_t lo_line, hi_line;   // march-axis faces: offset of x = 0 in the neighbour's ghost line
+  int64_t lo_side, hi_side;   // 3D side faces (y): per-plane offset base, -1 if none
+  int64_t w_col, e_col;       // x faces: neighbour ghost column base (add col(m)), -1 if none
+  int64_t lo_side_step, hi_side_step;
+};
+
+// MODE of the FP64 kernel
+enum { kModeSweep = 0, kModeResid = 1, kModeOuter = 2 };
+
+// Loader of "the field value" at an element offset: x, or x + e in the outer
+// refinement step (the updated iterate x_new = x + e, formed on the fly).
+template <int MODE, typename TE>
+struct F64Src {
+  const double* __restrict__ x;
+  const TE* __restrict__ e;
+  bool apply;
+
+  __device__ __forceinline__ double one(int64_t o) const {
+    double v = __ldg(x + o);
+    if constexpr (MODE == kModeOuter) {
+      if (apply) v = dadd(v, (double)to_f(e[o]));
+    }
+    return v;
+  }
+  __device__ __forceinline__ void two(int64_t o, bool valid, double& a, double& b) const {
+    if (!valid) {
+      a = 0.0;
+      b = 0.0;
+      return;
+    }
+    const double2 v = __ldg(reinterpret_cast<const double2*>(x + o));
+    a = v.x;
+    b = v.y;
+    if constexpr (MODE == kModeOuter) {
+      if (apply) {
+        a = dadd(a, (double)to_f(e[o]));
+        b = dadd(b, (double)to_f(e[o + 1]));
+      }
+    }
+  }
+};
+
+template <typename TR>
+__device__ __forceinline__ void store_r(TR* p, double r);
+template <>
+__device__ __forceinline__ void store_r<float>(float* p, double r) { *p = __double2float_rn(r); }
+template <>
+__device__ __forceinline__ void store_r<__nv_bfloat16>(__nv_bfloat16* p, double r) {
+  *p = __float2bfloat16_rn(__double2float_rn(r));
+}
+
+// ---------------------------------------------------------------------------
+// FP64 kernel: sweep (x' = t / 2d), residual only, or the refinement outer
+// step (x_new = x + e; r = b - A x_new; store x_new, r in low precision).
+// Two points per lane, 64 per warp row.
+
+template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads)
+k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
+      const SolveDev* __restrict__ solves, int epar) {
+  constexpr bool WRITE = MODE != kModeResid;
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (w >= nitems) return;
+  const WorkItem it = items[w];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  if (!S->active) return;
+  const int par = (S->phase + kpar) & 1;
+  F64Src<MODE, TE> src;
+  src.x = S->x[par];
+  src.e = MODE == kModeOuter ? reinterpret_cast<const TE*>(S->e[epar]) : nullptr;
+  src.apply = MODE == kModeOuter && S->apply_e;
+  double* __restrict__ xd = S->x[par ^ 1];
+  const double* __restrict__ f = S->f;
+  TR* __restrict__ rout = MODE == kModeOuter ? reinterpret_cast<TR*>(S->r) : nullptr;
+
+  const int y = it.y0;  // 3D: the fixed row
+  const Geo<DIM> G(B, y);
+  const int bx = B.bx;
+  const int xs = it.seg * kSegF64;
+  const int x = xs + 2 * lane;
+  const bool v0 = x < bx, v1 = x + 1 < bx;
+  const bool last0 = x == bx - 1, last1 = x + 1 == bx - 1;
+  const bool east_inner = x + 2 < bx;
+  const int64_t gW = B.xoff;
+  const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
+
+  PushTargets T;
+  if constexpr (PUSH && WRITE) {
+    const int lo = DIM == 2 ? 2 : 4, hi = lo + 1;
+    T.lo_line = T.hi_line = -1;
+    if (B.nbr[lo] >= 0) {
+      const BlockDev& N = blocks[B.nbr[lo]];
+      const Geo<DIM> GN(N, y);
+      T.lo_line = GN.line(GN.extent);
+    }
+    if (B.nbr[hi] >= 0) {
+      const BlockDev& N = blocks[B.nbr[hi]];
+      const Geo<DIM> GN(N, y);
+      T.hi_line = GN.line(-1);
+    }
+    T.lo_side = T.hi_side = -1;
+    if constexpr (DIM == 3) {
+      if (y == 0 && B.nbr[2] >= 0) {
+        const BlockDev& N = blocks[B.nbr[2]];
+        T.lo_side = N.off + (int64_t)(N.by + 1) * N.pitch;
+        T.lo_side_step = N.plane;
+      }
+      if (y == B.by - 1 && B.nbr[3] >= 0) {
+        const BlockDev& N = blocks[B.nbr[3]];
+        T.hi_side = N.off;
+        T.hi_side_step = N.plane;
+      }
+    }
+    T.w_col = T.e_col = -1;
+    if (B.nbr[0] >= 0) {
+      const BlockDev& N = blocks[B.nbr[0]];
+      T.w_col = N.xoff + (int64_t)N.by * N.bz;  // the west neighbour's east ghost column
+    }
+    if (B.nbr[1] >= 0) T.e_col = blocks[B.nbr[1]].xoff;  // the east neighbour's west column
+  }
+
+  const int m0 = DIM == 2 ? it.y0 : it.z0;
+  const int mend = m0 + it.n;
+  int m = m0;
+
+  // lines m-1 (prev) and m (cur)
+  double p0, p1, c0, c1;
+  src.two(G.line(m - 1) + x, v0, p0, p1);
+  src.two(G.line(m) + x, v0, c0, c1);
+  // prologue pairs of line m-1: A0p = P(m-1, x) = p[x+1] + c[x]; A1p = P(m-1, x+1)
+  double pE = __shfl_down_sync(FULL_MASK, p0, 1);
+  if (lane == 31 && east_inner) pE = src.one(G.line(m - 1) + x + 2);
+  double A0p = dadd(p1, c0);
+  double A1p = dadd(pE, c1);
+
+  for (; m < mend; ++m) {
+    const int64_t lc = G.line(m);
+    const int col = G.col(m);
+    if (last0) c1 = src.one(gE + col);
+    double n0, n1;
+    src.two(G.line(m + 1) + x, v0, n0, n1);
+    double f0 = 0.0, f1 = 0.0;
+    if (v0) {
+      const double2 fv = __ldg(reinterpret_cast<const double2*>(f + lc + x));
+      f0 = fv.x;
+      f1 = fv.y;
+    }
+    double sn0 = 0.0, sn1 = 0.0;
+    if constexpr (DIM == 3) {
+      double a0, a1, b0_, b1_;
+      src.two(lc - G.side + x, v0, a0, a1);
+      src.two(lc + G.side + x, v0, b0_, b1_);
+      sn0 = dadd(a0, b0_);
+      sn1 = dadd(a1, b1_);
+    }
+    // east neighbour of point x+1 on line m
+    double e1 = __shfl_down_sync(FULL_MASK, c0, 1);
+    if (lane == 31 && east_inner) e1 = src.one(lc + x + 2);
+    if (last1) e1 = src.one(gE + col);
+    // (W + S) pair of point x: from the left lane, or formed here on lane 0
+    double bw = __shfl_up_sync(FULL_MASK, A1p, 1);
+    if (lane == 0) {
+      const double wv = xs > 0 ? src.one(lc + xs - 1) : src.one(gW + col);
+      bw = dadd(wv, p0);
+    }
+    const double A0 = dadd(c1, n0);  // P(m, x)   = c[x+1] + n[x]
+    const double A1 = dadd(e1, n1);  // P(m, x+1) = c[x+2] + n[x+1]
+    double t0 = dadd(bw, A0), t1 = dadd(A0p, A1);
+    if constexpr (DIM == 3) {
+      t0 = dadd(t0, sn0);
+      t1 = dadd(t1, sn1);
+    }
+    t0 = dadd(t0, f0);
+    t1 = dadd(t1, f1);
+
+    if constexpr (WRITE) {
+      double o0, o1;
+      if constexpr (MODE == kModeSweep) {
+        o0 = jdiv<DIM>(t0);
+        o1 = jdiv<DIM>(t1);
+      } else {
+        o0 = c0;  // outer step: the updated iterate itself
+        o1 = c1;
+      }
+      double* d = xd + lc + x;
+      if (v1) *reinterpret_cast<double2*>(d) = make_double2(o0, o1);
+      else if (v0) *d = o0;
+      if constexpr (PUSH) {
+        if (m == 0 && T.lo_line >= 0) {
+          if (v1) *reinterpret_cast<double2*>(xd + T.lo_line + x) = make_double2(o0, o1);
+          else if (v0) xd[T.lo_line + x] = o0;
+        }
+        if (m == G.extent - 1 && T.hi_line >= 0) {
+          if (v1) *reinterpret_cast<double2*>(xd + T.hi_line + x) = make_double2(o0, o1);
+          else if (v0) xd[T.hi_line + x] = o0;
+        }
+        if constexpr (DIM == 3) {
+          if (T.lo_side >= 0) {
+            double* q = xd + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x;
+            if (v1) *reinterpret_cast<double2*>(q) = make_double2(o0, o1);
+            else if (v0) *q = o0;
+          }
+          if (T.hi_side >= 0) {
+            double* q = xd + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x;
+            if (v1) *reinterpret_cast<double2*>(q) = make_double2(o0, o1);
+            else if (v0) *q = o0;
+          }
+        }
+        if (x == 0 && T.w_col >= 0) xd[T.w_col + col] = o0;
+        if (T.e_col >= 0) {
+          if (last0) xd[T.e_col + col] = o0;
+          if (last1) xd[T.e_col + col] = o1;
+        }
+      }
+    }
+    if constexpr (RESID || MODE == kModeOuter) {
+      const double twod = DIM == 2 ? 4.0 : 6.0;
+      const double r0 = __dsub_rn(t0, __dmul_rn(twod, c0));
+      const double r1 = __dsub_rn(t1, __dmul_rn(twod, c1));
+      if constexpr (MODE == kModeOuter) {
+        if (v1) {
+          store_r<TR>(rout + lc + x, r0);
+          store_r<TR>(rout + lc + x + 1, r1);
+        } else if (v0) {
+          store_r<TR>(rout + lc + x, r0);
+        }
+      }
+      if constexpr (RESID) {
+        double q = v0 ? __dmul_rn(r0, r0) : 0.0;
+        if (v1) q = dadd(q, __dmul_rn(r1, r1));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) q = dadd(q, __shfl_xor_sync(FULL_MASK, q, o));
+        if (lane == 0) {
+          const int64_t row = DIM == 2 ? (int64_t)(B.oy + m) : (int64_t)(B.oz + m) * S->ny + (B.oy + y);
+          S->part[B.part + row * S->part_row + it.seg] = q;
+        }
+      }
+    }
+    A0p = A0;
+    A1p = A1;
+    p0 = c0;
+    p1 = c1;
+    c0 = n0;
+    c1 = n1;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Low-precision inner sweep of the refinement: A e = r with zero Dirichlet
+// ghosts, FP32 arithmetic, e stored as TE (float or bfloat16, RNE), r read as
+// TR.  Four points per lane, 128 per warp row.  FIRST: the input e is zero,
+// so only r is read (e' = (0 + r) / 2d).
+
+template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads)
+k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
+      const SolveDev* __restrict__ solves, int epar) {
+  const int lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (w >= nitems) return;
+  const WorkItem it = items[w];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  if (!S->active) return;
+  const TE* __restrict__ es = reinterpret_cast<const TE*>(S->e[epar ^ 1]);
+  TE* __restrict__ ed = reinterpret_cast<TE*>(S->e[epar]);
+  const TR* __restrict__ rr = reinterpret_cast<const TR*>(S->r);
+
+  const int y = it.y0;
+  const Geo<DIM> G(B, y);
+  const int bx = B.bx;
+  const int xs = it.seg * kSegLow;
+  const int x = xs + 4 * lane;
+  const int nvalid = bx - x;  // > 0 when the lane holds points
+  const bool any = nvalid > 0;
+  const int64_t gW = B.xoff;
+  const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
+
+  PushTargets T;
+  if constexpr (PUSH) {
+    const int lo = DIM == 2 ? 2 : 4, hi = lo + 1;
+    T.lo_line = T.hi_line = -1;
+    if (B.nbr[lo] >= 0) {
+      const BlockDev& N = blocks[B.nbr[lo]];
+      const Geo<DIM> GN(N, y);
+      T.lo_line = GN.line(GN.extent);
+    }
+    if (B.nbr[hi] >= 0) {
+      const BlockDev& N = blocks[B.nbr[hi]];
+      const Geo<DIM> GN(N, y);
+      T.hi_line = GN.line(-1);
+    }
+    T.lo_side = T.hi_side = -1;
+    if constexpr (DIM == 3) {
+      if (y == 0 && B.nbr[2] >= 0) {
+        const BlockDev& N = blocks[B.nbr[2]];
+        T.lo_side = N.off + (int64_t)(N.by + 1) * N.pitch;
+        T.lo_side_step = N.plane;
+      }
+      if (y == B.by - 1 && B.nbr[3] >= 0) {
+        const BlockDev& N = blocks[B.nbr[3]];
+        T.hi_side = N.off;
+        T.hi_side_step = N.plane;
+      }
+    }
+    T.w_col = T.e_col = -1;
+    if (B.nbr[0] >= 0) {
+      const BlockDev& N = blocks[B.nbr[0]];
+      T.w_col = N.xoff + (int64_t)N.by * N.bz;
+    }
+    if (B.nbr[1] >= 0) T.e_col = blocks[B.nbr[1]].xoff;
+  }
+
+  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  const int m0 = DIM == 2 ? it.y0 : it.z0;
+  const int mend = m0 + it.n;
+  float4 p = zero4, c = zero4;
+  if constexpr (!FIRST) {
+    if (any) {
+      p = ld4(es + G.line(m0 - 1) + x);
+      c = ld4(es + G.line(m0) + x);
+    }
+  }
+  for (int m = m0; m < mend; ++m) {
+    const int64_t lc = G.line(m);
+    const int col = G.col(m);
+    float4 n = zero4, rv = zero4;
+    if (any) rv = ld4(rr + lc + x);
+    float4 o;
+    if constexpr (FIRST) {
+      o.x = jdivf<DIM>(__fadd_rn(0.0f, rv.x));
+      o.y = jdivf<DIM>(__fadd_rn(0.0f, rv.y));
+      o.z = jdivf<DIM>(__fadd_rn(0.0f, rv.z));
+      o.w = jdivf<DIM>(__fadd_rn(0.0f, rv.w));
+    } else {
+      if (any) n = ld4(es + G.line(m + 1) + x);
+      float4 sa = zero4, sb = zero4;
+      if constexpr (DIM == 3) {
+        if (any) {
+          sa = ld4(es + lc - G.side + x);
+          sb = ld4(es + lc + G.side + x);
+        }
+      }
+      // west of point 0, east of point 3
+      float wv = __shfl_up_sync(FULL_MASK, c.w, 1);
+      if (lane == 0) wv = xs > 0 ? to_f(es[lc + xs - 1]) : to_f(es[gW + col]);
+      float ev = __shfl_down_sync(FULL_MASK, c.x, 1);
+      if (lane == 31 && x + 4 < bx) ev = to_f(es[lc + x + 4]);
+      // the lane holding the block's last point takes the east ghost
+      float ge = 0.f;
+      if (any && nvalid <= 4) ge = to_f(es[gE + col]);
+      const float cc[6] = {wv, c.x, c.y, c.z, c.w, ev};
+      float ov[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const float east = (k + 1 == nvalid) ? ge : cc[k + 2];  // the block's last point takes the ghost
+        float t = __fadd_rn(__fadd_rn(cc[k], comp(p, k)), __fadd_rn(east, comp(n, k)));
+        if constexpr (DIM == 3) t = __fadd_rn(t, __fadd_rn(comp(sa, k), comp(sb, k)));
+        t = __fadd_rn(t, comp(rv, k));
+        ov[k] = jdivf<DIM>(t);
+      }
+      o = make_float4(ov[0], ov[1], ov[2], ov[3]);
+    }
+    if (any) {
+      st4_valid<TE>(ed + lc + x, o, nvalid);
+      if constexpr (PUSH) {
+        if (m == 0 && T.lo_line >= 0) st4_valid<TE>(ed + T.lo_line + x, o, nvalid);
+        if (m == G.extent - 1 && T.hi_line >= 0) st4_valid<TE>(ed + T.hi_line + x, o, nvalid);
+        if constexpr (DIM == 3) {
+          if (T.lo_side >= 0) st4_valid<TE>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
+          if (T.hi_side >= 0) st4_valid<TE>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
+        }
+        if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o.x);
+        if (nvalid <= 4 && T.e_col >= 0) ed[T.e_col + col] = from_f<TE>(comp(o, nvalid - 1));
+      }
+    }
+    if constexpr (!FIRST) {
+      p = c;
+      c = n;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Standalone halo exchange (section 4.3: pack the GPU faces, move them, unpack
+// them into the halo).  One CTA per (block, face); domain faces are skipped.
+// Face element order: x faces (z, y), y faces (z, x), z faces (y, x), lowest
+// axis fastest.
+
+__device__ __forceinline__ int64_t face_elem(const BlockDev& B, int face, int i, bool ghost) {
+  // offset of element i of face `face` of block B: its boundary layer
+  // (ghost = false) or its ghost layer (ghost = true)
+  const int axis = face >> 1, hi = face & 1;
+  if (axis == 0) {
+    const int y = i % B.by, z = i / B.by;
+    if (ghost) return (hi ? B.xoff + (int64_t)B.by * B.bz : B.xoff) + (int64_t)z * B.by + y;
+    const int x = hi ? B.bx - 1 : 0;
+    return B.off + (int64_t)(z + B.gz) * B.plane + (int64_t)(y + 1) * B.pitch + x;
+  }
+  if (axis == 1) {
+    const int x = i % B.bx, z = i / B.bx;
+    const int y = ghost ? (hi ? B.by : -1) : (hi ? B.by - 1 : 0);
+    return B.off + (int64_t)(z + B.gz) * B.plane + (int64_t)(y + 1) * B.pitch + x;
+  }
+  const int x = i % B.bx, y = i / B.bx;
+  const int z = ghost ? (hi ? B.bz : -1) : (hi ? B.bz - 1 : 0);
+  return B.off + (int64_t)(z + 1) * B.plane + (int64_t)(y + 1) * B.pitch + x;
+}
+
+__device__ __forceinline__ int64_t face_send_off(const BlockDev& B, int face) {
+  int64_t o = B.foff;
+  for (int k = 0; k < face; ++k) o += B.fsz[k];
+  return o;
+}
+
+template <typename T>
+__global__ void k_halo_pack(const FaceItem* __restrict__ items, const BlockDev* __restrict__ blocks,
+                            const SolveDev* __restrict__ solves, int which, int par) {
+  const FaceItem it = items[blockIdx.x];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  if (!S->active || B.nbr[it.face] < 0) return;
+  // which = 0: the FP64 iterate x[(phase + par) & 1]; which = 1: e[par]
+  const T* a = which == 0 ? reinterpret_cast<const T*>(S->x[(S->phase + par) & 1])
+                          : reinterpret_cast<const T*>(S->e[par]);
+  T* send = which == 0 ? reinterpret_cast<T*>(S->send64) : reinterpret_cast<T*>(S->sendlo);
+  const int64_t so = face_send_off(B, it.face);
+  const int n = B.fsz[it.face];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) send[so + i] = a[face_elem(B, it.face, i, false)];
+}
+
+template <typename T>
+__global__ void k_halo_unpack(const FaceItem* __restrict__ items, const BlockDev* __restrict__ blocks,
+                              const SolveDev* __restrict__ solves, int which, int par) {
+  const FaceItem it = items[blockIdx.x];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  const int nb = B.nbr[it.face];
+  if (!S->active || nb < 0) return;
+  const BlockDev N = blocks[nb];
+  T* a = which == 0 ? reinterpret_cast<T*>(S->x[(S->phase + par) & 1]) : reinterpret_cast<T*>(S->e[par]);
+  const T* send = which == 0 ? reinterpret_cast<const T*>(S->send64) : reinterpret_cast<const T*>(S->sendlo);
+  const int64_t so = face_send_off(N, it.face ^ 1);  // the neighbour's opposite face
+  const int n = B.fsz[it.face];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a[face_elem(B, it.face, i, true)] = send[so + i];
+}
+
+// ---------------------------------------------------------------------------
+// Deterministic residual reduction: CTA c of a solve sums its chunk of
+// partials in a fixed order (thread-strided, then a shared-memory tree); the
+// last CTA of the solve to finish sums the chunk results in a fixed order.
+// The result depends only on the partials, never on scheduling.
+
+__global__ void __launch_bounds__(kRedThreads)
+k_reduce(const RedItem* __restrict__ items, SolveDev* __restrict__ solves) {
+  __shared__ double sm[kRedThreads];
+  __shared__ int is_last;
+  const RedItem it = items[blockIdx.x];
+  SolveDev* S = solves + it.solve;
+  if (!S->active) return;
+  const int t = threadIdx.x;
+  double acc = 0.0;
+  const double* part = S->part + it.start;
+  for (int i = t; i < it.len; i += kRedThreads) acc = dadd(acc, part[i]);
+  sm[t] = acc;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (t < s) sm[t] = dadd(sm[t], sm[t + s]);
+    __syncthreads();
+  }
+  if (t == 0) {
+    S->lvl1[it.chunk] = sm[0];
+    __threadfence();
+    const unsigned tk = atomicAdd(S->ticket, 1u);
+    is_last = tk == (unsigned)(it.nchunks - 1);
+  }
+  __syncthreads();
+  if (!is_last) return;
+  __threadfence();
+  acc = 0.0;
+  for (int i = t; i < it.nchunks; i += kRedThreads) acc = dadd(acc, __ldcg(S->lvl1 + i));
+  sm[t] = acc;
+  __syncthreads();
+  for (int s = kRedThreads / 2; s > 0; s >>= 1) {
+    if (t < s) sm[t] = dadd(sm[t], sm[t + s]);
+    __syncthreads();
+  }
+  if (t == 0) {
+    S->rss[0] = sm[0];
+    *S->ticket = 0u;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Dense (interior, x fastest) <-> blocked copies; one warp per block row.
+
+__global__ void k_scatter(const RowItem* __restrict__ items, int n, const BlockDev* __restrict__ blocks,
+                          SolveDev* __restrict__ solves, const double* __restrict__ dense, int which, int par,
+                          int64_t nx, int64_t ny) {
+  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (w >= n) return;
+  const RowItem it = items[w];
+  const BlockDev B = blocks[it.block];
+  SolveDev* S = solves + B.solve;
+  double* a = which == 0 ? S->x[(S->phase + par) & 1] : S->f;
+  const int64_t o = B.off + (int64_t)(it.z + B.gz) * B.plane + (int64_t)(it.y + 1) * B.pitch;
+  const int64_t d = ((int64_t)(B.oz + it.z) * ny + (B.oy + it.y)) * nx + B.ox;
+  for (int x = threadIdx.x & 31; x < B.bx; x += 32) a[o + x] = dense[d + x];
+}
+
+__global__ void k_gather(const RowItem* __restrict__ items, int n, const BlockDev* __restrict__ blocks,
+                         const SolveDev* __restrict__ solves, double* __restrict__ dense, int par, int64_t nx,
+                         int64_t ny) {
+  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (w >= n) return;
+  const RowItem it = items[w];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  const double* a = S->x[(S->phase + par) & 1];
+  const int64_t o = B.off + (int64_t)(it.z + B.gz) * B.plane + (int64_t)(it.y + 1) * B.pitch;
+  const int64_t d = ((int64_t)(B.oz + it.z) * ny + (B.oy + it.y)) * nx + B.ox;
+  for (int x = threadIdx.x & 31; x < B.bx; x += 32) dense[d + x] = a[o + x];
+}
+
+// Dirichlet values g into the domain-boundary ghosts of x[par].
+struct FacePtrs {
+  const double* f[6];
+};
+
+__global__ void k_ghost_fill(const FaceItem* __restrict__ items, const BlockDev* __restrict__ blocks,
+                             SolveDev* __restrict__ solves, FacePtrs faces, int par, int64_t nx, int64_t ny,
+                             int64_t nz) {
+  const FaceItem it = items[blockIdx.x];
+  const BlockDev B = blocks[it.block];
+  if (B.nbr[it.face] >= 0) return;
+  SolveDev* S = solves + B.solve;
+  double* a = S->x[par];
+  const double* g = faces.f[it.face];
+  const int axis = it.face >> 1;
+  const int n = B.fsz[it.face];
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    int64_t gi;
+    if (axis == 0) {
+      const int y = i % B.by, z = i / B.by;
+      gi = (int64_t)(B.oy + y) + ny * (B.oz + z);
+    } else if (axis == 1) {
+      const int x = i % B.bx, z = i / B.bx;
+      gi = (int64_t)(B.ox + x) + nx * (B.oz + z);
+    } else {
+      const int x = i % B.bx, y = i / B.bx;
+      gi = (int64_t)(B.ox + x) + nx * (B.oy + y);
+    }
+    a[face_elem(B, it.face, i, true)] = g ? g[gi] : 0.0;
+  }
+  (void)nz;
+}
+
+__global__ void k_phase_advance(SolveDev* solves, int n, int dphase, int set_apply_e) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  SolveDev* S = solves + i;
+  if (!S->active) return;
+  S->phase = (S->phase + dphase) & 1;
+  if (set_apply_e >= 0) S->apply_e = set_apply_e;
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers
+
+static inline int grid_of(int items, int per) { return (items + per - 1) / per; }
+
+template <int DIM>
+static int sweep_f64_dim(const Tables& t, int kpar, bool push, bool resid, bool write, cudaStream_t s) {
+  const dim3 g(grid_of(t.n64, kWarps)), b(kThreads);
+  if (t.n64 == 0) return 0;
+  if (!write) {
+    k_f64<DIM, kModeResid, false, true, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
+  } else if (push) {
+    if (resid) k_f64<DIM, kModeSweep, true, true, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
+    else k_f64<DIM, kModeSweep, true, false, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
+  } else {
+    if (resid) k_f64<DIM, kModeSweep, false, true, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
+    else k_f64<DIM, kModeSweep, false, false, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
+  }
+  return (int)cudaGetLastError();
+}
+
+int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  return t.ndim == 2 ? sweep_f64_dim<2>(t, kpar, push, resid, write, s)
+                     : sweep_f64_dim<3>(t, kpar, push, resid, write, s);
+}
+
+template <int DIM, typename TE, typename TR>
+static int low_typed(const Tables& t, int epar, bool first, bool push, cudaStream_t s) {
+  const dim3 g(grid_of(t.nlo, kWarps)), b(kThreads);
+  if (t.nlo == 0) return 0;
+  if (first) {
+    if (push) k_low<DIM, true, true, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+    else k_low<DIM, true, false, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+  } else {
+    if (push) k_low<DIM, false, true, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+    else k_low<DIM, false, false, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+  }
+  return (int)cudaGetLastError();
+}
+
+template <int DIM>
+static int low_dim(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, cudaStream_t s) {
+  if (low == kLowF32) return low_typed<DIM, float, float>(t, epar, first, push, s);
+  if (r_bf16) return low_typed<DIM, __nv_bfloat16, __nv_bfloat16>(t, epar, first, push, s);
+  return low_typed<DIM, __nv_bfloat16, float>(t, epar, first, push, s);
+}
+
+int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  return t.ndim == 2 ? low_dim<2>(t, epar, first, push, low, r_bf16, s)
+                     : low_dim<3>(t, epar, first, push, low, r_bf16, s);
+}
+
+template <int DIM, typename TE, typename TR>
+static int outer_typed(const Tables& t, int epar_last, bool push, cudaStream_t s) {
+  const dim3 g(grid_of(t.n64, kWarps)), b(kThreads);
+  if (t.n64 == 0) return 0;
+  if (push) k_f64<DIM, kModeOuter, true, true, TE, TR><<<g, b, 0, s>>>(t.w64, t.n64, 0, t.blocks, t.solves, epar_last);
+  else k_f64<DIM, kModeOuter, false, true, TE, TR><<<g, b, 0, s>>>(t.w64, t.n64, 0, t.blocks, t.solves, epar_last);
+  return (int)cudaGetLastError();
+}
+
+template <int DIM>
+static int outer_dim(const Tables& t, int epar_last, bool push, int low, bool r_bf16, cudaStream_t s) {
+  if (low == kLowF32) return outer_typed<DIM, float, float>(t, epar_last, push, s);
+  if (r_bf16) return outer_typed<DIM, __nv_bfloat16, __nv_bfloat16>(t, epar_last, push, s);
+  return outer_typed<DIM, __nv_bfloat16, float>(t, epar_last, push, s);
+}
+
+int launch_refine_outer(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  return t.ndim == 2 ? outer_dim<2>(t, epar_last, push, low, r_bf16, s)
+                     : outer_dim<3>(t, epar_last, push, low, r_bf16, s);
+}
+
+int launch_halo_pack(const Tables& t, int which, int par, int low, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.nfaces == 0) return 0;
+  if (which == 0) k_halo_pack<double><<<t.nfaces, 256, 0, s>>>(t.faces, t.blocks, t.solves, 0, par);
+  else if (low == kLowF32) k_halo_pack<float><<<t.nfaces, 256, 0, s>>>(t.faces, t.blocks, t.solves, 1, par);
+  else k_halo_pack<__nv_bfloat16><<<t.nfaces, 256, 0, s>>>(t.faces, t.blocks, t.solves, 1, par);
+  return (int)cudaGetLastError();
+}
+
+int launch_halo_unpack(const Tables& t, int which, int par, int low, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.nfaces == 0) return 0;
+  if (which == 0) k_halo_unpack<double><<<t.nfaces, 256, 0, s>>>(t.faces, t.blocks, t.solves, 0, par);
+  else if (low == kLowF32) k_halo_unpack<float><<<t.nfaces, 256, 0, s>>>(t.faces, t.blocks, t.solves, 1, par);
+  else k_halo_unpack<__nv_bfloat16><<<t.nfaces, 256, 0, s>>>(t.faces, t.blocks, t.solves, 1, par);
+  return (int)cudaGetLastError();
+}
+
+int launch_reduce(const Tables& t, void* stream) {
+  if (t.nred == 0) return 0;
+  k_reduce<<<t.nred, kRedThreads, 0, (cudaStream_t)stream>>>(t.red, t.solves);
+  return (int)cudaGetLastError();
+}
+
+int launch_scatter(const Tables& t, const double* dense, int which, int par, int64_t nx, int64_t ny, void* stream) {
+  if (t.nrows == 0) return 0;
+  k_scatter<<<grid_of(t.nrows, kWarps), kThreads, 0, (cudaStream_t)stream>>>(t.rows, t.nrows, t.blocks, t.solves,
+                                                                                dense, which, par, nx, ny);
+  return (int)cudaGetLastError();
+}
+
+int launch_gather(const Tables& t, double* dense, int par, int64_t nx, int64_t ny, void* stream) {
+  if (t.nrows == 0) return 0;
+  k_gather<<<grid_of(t.nrows, kWarps), kThreads, 0, (cudaStream_t)stream>>>(t.rows, t.nrows, t.blocks, t.solves,
+                                                                               dense, par, nx, ny);
+  return (int)cudaGetLastError();
+}
+
+int launch_ghost_fill(const Tables& t, const double* const* faces_dev, int par, int64_t nx, int64_t ny, int64_t nz,
+                      void* stream) {
+  if (t.nfaces == 0) return 0;
+  FacePtrs fp;
+  for (int i = 0; i < 6; ++i) fp.f[i] = faces_dev[i];
+  k_ghost_fill<<<t.nfaces, 256, 0, (cudaStream_t)stream>>>(t.faces, t.blocks, t.solves, fp, par, nx, ny, nz);
+  return (int)cudaGetLastError();
+}
+
+int launch_phase_advance(SolveDev* solves, int nsolves, int dphase, int set_apply_e, void* stream) {
+  if (nsolves == 0) return 0;
+  k_phase_advance<<<grid_of(nsolves, 256), 256, 0, (cudaStream_t)stream>>>(solves, nsolves, dphase, set_apply_e);
+  return (int)cudaGetLastError();
+}
+
+}  // namespace jgb

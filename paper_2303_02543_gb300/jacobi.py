@@ -1,0 +1,323 @@
+"""Thin Python binding of the C ABI in include/jacobi.h (argument marshalling
+only: every step of the Jacobi path runs in the CUDA library).
+
+The functions named ``jacobi_*`` mirror the C entry points one to one; the
+``Solver`` class wraps them for convenience.  PyTorch supplies the device
+memory (the library's allocations are routed to torch's caching allocator)
+and the stream (torch's current stream).  There is no CPU fallback: if the
+CUDA library is missing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import sys
+
+import numpy as np
+
+from . import build as _build
+
+F64, F32_REFINE, BF16_REFINE = 0, 1, 2
+DTYPES = {"f64": F64, "f32_refine": F32_REFINE, "bf16_refine": BF16_REFINE}
+BC_ZERO, BC_CONST, BC_FACES = 0, 1, 2
+
+STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NOT_CONVERGED",
+          5: "ERR_DIVERGED", 6: "ERR_TIMEOUT", 7: "ERR_BUSY"}
+OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT, ERR_BUSY = range(8)
+
+# Every symbol declared in include/jacobi.h.
+EXPORTS = ["jacobi_set_allocator", "jacobi_create", "jacobi_sweep", "jacobi_residual", "jacobi_solve",
+           "jacobi_get_field", "jacobi_set_field", "jacobi_set_source", "jacobi_set_option",
+           "jacobi_get_option", "jacobi_profile", "jacobi_device_bytes", "jacobi_destroy",
+           "jacobi_last_error", "jacobi_version"]
+
+
+class JacobiError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{STATUS.get(status, status)}: {message}")
+        self.status = status
+
+
+class Boundary(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("value", ctypes.c_double), ("faces", ctypes.c_void_p * 6)]
+
+
+_lib = None
+_alloc_cb = None
+_free_cb = None
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or library_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library {path} is missing; build it with "
+                           "`python -m paper_2303_02543_gb300.build` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    vp, i64, i64p, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_double)
+    sig = {
+        "jacobi_set_allocator": (None, [ALLOC_FN, FREE_FN, vp]),
+        "jacobi_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, i64p, i64p, ctypes.c_int,
+                                          ctypes.POINTER(Boundary), vp, vp, vp]),
+        "jacobi_sweep": (ctypes.c_int, [vp, i64]),
+        "jacobi_residual": (ctypes.c_int, [vp, dp, dp]),
+        "jacobi_solve": (ctypes.c_int, [vp, ctypes.c_double, i64, i64p, dp]),
+        "jacobi_get_field": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "jacobi_set_field": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "jacobi_set_source": (ctypes.c_int, [vp, vp, ctypes.c_int]),
+        "jacobi_set_option": (ctypes.c_int, [vp, ctypes.c_char_p, i64]),
+        "jacobi_get_option": (ctypes.c_int, [vp, ctypes.c_char_p, i64p]),
+        "jacobi_profile": (ctypes.c_int, [vp, ctypes.c_char_p, dp, i64p, ctypes.c_int]),
+        "jacobi_device_bytes": (ctypes.c_int, [vp, i64p]),
+        "jacobi_destroy": (None, [vp]),
+        "jacobi_last_error": (ctypes.c_char_p, [vp]),
+        "jacobi_version": (ctypes.c_int, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def use_torch_allocator(enable: bool = True):
+    """Route the library's device allocations through torch's caching allocator."""
+    global _alloc_cb, _free_cb
+    lib = load()
+    if not enable:
+        lib.jacobi_set_allocator(ALLOC_FN(), FREE_FN(), None)
+        return
+    import torch
+
+    def _alloc(nbytes, stream, _user):
+        try:
+            return int(torch.cuda.caching_allocator_alloc(int(nbytes), device=torch.cuda.current_device(),
+                                                          stream=int(stream or 0)))
+        except Exception:  # noqa: BLE001 - reported to C as a NULL allocation (JACOBI_ERR_OOM)
+            return None
+
+    def _free(ptr, _stream, _user):
+        if ptr and not sys.is_finalizing():
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+    _alloc_cb, _free_cb = ALLOC_FN(_alloc), FREE_FN(_free)
+    lib.jacobi_set_allocator(_alloc_cb, _free_cb, None)
+
+
+def _check(status, handle=None):
+    if status != OK:
+        msg = load().jacobi_last_error(handle)
+        raise JacobiError(status, msg.decode() if msg else "")
+    return status
+
+
+def _ptr(a):
+    """Host numpy array or torch CUDA tensor -> (pointer, on_device)."""
+    if a is None:
+        return None, 0
+    if hasattr(a, "data_ptr"):  # torch tensor: device or (pinned) host memory
+        return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    return ctypes.c_void_p(a.ctypes.data), 0
+
+
+def default_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+# ---- C entry points, one to one -------------------------------------------
+
+def jacobi_version():
+    return load().jacobi_version()
+
+
+def jacobi_create(ndim, dims, block, dtype, bc=None, source=None, x0=None, stream=None):
+    lib = load()
+    dl, bl = list(dims)[:3], list(block)[:3]  # the C side validates ndim against 2..3
+    d = (ctypes.c_int64 * 3)(*(dl + [1] * (3 - len(dl))))
+    b = (ctypes.c_int64 * 3)(*(bl + [1] * (3 - len(bl))))
+    h = ctypes.c_void_p()
+    st = lib.jacobi_create(ctypes.byref(h), ndim, d, b, dtype, None if bc is None else ctypes.byref(bc),
+                           source, x0, stream)
+    _check(st, None)
+    return h
+
+
+def jacobi_sweep(h, n):
+    return _check(load().jacobi_sweep(h, int(n)), h)
+
+
+def jacobi_residual(h):
+    rel, ab = ctypes.c_double(), ctypes.c_double()
+    _check(load().jacobi_residual(h, ctypes.byref(rel), ctypes.byref(ab)), h)
+    return rel.value, ab.value
+
+
+def jacobi_solve(h, tol, max_sweeps):
+    sw, rel = ctypes.c_int64(), ctypes.c_double()
+    st = load().jacobi_solve(h, float(tol), int(max_sweeps), ctypes.byref(sw), ctypes.byref(rel))
+    if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
+        _check(st, h)
+    return st, sw.value, rel.value
+
+
+def jacobi_get_field(h, out_ptr, on_device):
+    return _check(load().jacobi_get_field(h, out_ptr, int(on_device)), h)
+
+
+def jacobi_set_field(h, in_ptr, on_device):
+    return _check(load().jacobi_set_field(h, in_ptr, int(on_device)), h)
+
+
+def jacobi_set_source(h, in_ptr, on_device):
+    return _check(load().jacobi_set_source(h, in_ptr, int(on_device)), h)
+
+
+def jacobi_set_option(h, key, value):
+    return _check(load().jacobi_set_option(h, key.encode(), int(value)), h)
+
+
+def jacobi_get_option(h, key):
+    v = ctypes.c_int64()
+    _check(load().jacobi_get_option(h, key.encode(), ctypes.byref(v)), h)
+    return v.value
+
+
+def jacobi_profile(h, kernel, reset=False):
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    _check(load().jacobi_profile(h, kernel.encode(), ctypes.byref(ms), ctypes.byref(n), int(bool(reset))), h)
+    return ms.value, n.value
+
+
+def jacobi_device_bytes(h):
+    v = ctypes.c_int64()
+    _check(load().jacobi_device_bytes(h, ctypes.byref(v)), h)
+    return v.value
+
+
+def jacobi_destroy(h):
+    if h:
+        load().jacobi_destroy(h)
+
+
+def jacobi_last_error(h=None):
+    m = load().jacobi_last_error(h)
+    return m.decode() if m else ""
+
+
+# ---- convenience wrapper -------------------------------------------------
+
+def make_boundary(faces=None, value=None):
+    """Boundary struct from a list of face arrays (host) or a constant."""
+    bc = Boundary()
+    keep = []
+    if faces is not None:
+        bc.kind = BC_FACES
+        for i, f in enumerate(faces):
+            if f is None:
+                bc.faces[i] = None
+                continue
+            arr = np.ascontiguousarray(f, dtype=np.float64)
+            keep.append(arr)
+            bc.faces[i] = arr.ctypes.data
+    elif value is not None:
+        bc.kind, bc.value = BC_CONST, float(value)
+    else:
+        bc.kind = BC_ZERO
+    return bc, keep
+
+
+class Solver:
+    """One grid: Solver(dims, block, dtype="f64", faces=..., source=..., x0=...)."""
+
+    def __init__(self, dims, block, dtype="f64", faces=None, bc_value=None, source=None, x0=None,
+                 stream=None, torch_alloc=True, **options):
+        self.dims = tuple(int(d) for d in dims)
+        self.ndim = len(self.dims)
+        self.shape = tuple(reversed(self.dims))
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        if torch_alloc:
+            use_torch_allocator(True)
+        bc, keep = make_boundary(faces, bc_value)
+        src = None if source is None else np.ascontiguousarray(source, dtype=np.float64)
+        xx = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        self.stream = default_stream() if stream is None else stream
+        self.h = jacobi_create(self.ndim, self.dims, block, self.dtype, bc,
+                               None if src is None else src.ctypes.data,
+                               None if xx is None else xx.ctypes.data, self.stream)
+        del keep
+        for k, v in options.items():
+            self.set_option(k, v)
+
+    def sweep(self, n):
+        jacobi_sweep(self.h, n)
+
+    def residual(self):
+        return jacobi_residual(self.h)
+
+    def solve(self, tol, max_sweeps):
+        return jacobi_solve(self.h, tol, max_sweeps)
+
+    def field(self, out=None):
+        if out is None:
+            out = np.empty(self.shape, dtype=np.float64)
+        p, dev = _ptr(out)
+        jacobi_get_field(self.h, p, dev)
+        return out
+
+    def set_field(self, x):
+        if not hasattr(x, "data_ptr"):
+            x = np.ascontiguousarray(x, dtype=np.float64)
+        p, dev = _ptr(x)
+        jacobi_set_field(self.h, p, dev)
+
+    def set_source(self, f):
+        if not hasattr(f, "data_ptr"):
+            f = np.ascontiguousarray(f, dtype=np.float64)
+        p, dev = _ptr(f)
+        jacobi_set_source(self.h, p, dev)
+
+    def set_option(self, key, value):
+        jacobi_set_option(self.h, key, value)
+
+    def get_option(self, key):
+        return jacobi_get_option(self.h, key)
+
+    def profile(self, kernel, reset=False):
+        return jacobi_profile(self.h, kernel, reset)
+
+    def device_bytes(self):
+        return jacobi_device_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            jacobi_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        if not sys.is_finalizing():
+            try:
+                self.close()
+            except Exception:  # noqa: BLE001
+                pass

@@ -1,0 +1,278 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Readings (section 4.3's Jacobi proxy): FP64 sweeps in the canonical order
+are bit-identical to the oracle (gate: 1e-13 relative per point); the
+over-decomposed sweep (section 4.4) is bit-identical to the monolithic one;
+refinement solves reach a relative residual <= 1e-8 checked by the oracle.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_02543_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2303_02543_gb300 import jacobi as J  # noqa: E402
+
+
+def per_point_close(g, c, rtol=1e-13):
+    """|g - c| <= rtol * max(|c|, 1e-3 ||c||_inf) at every point."""
+    scale = np.maximum(np.abs(c), 1e-3 * np.max(np.abs(c)) + 1e-300)
+    return np.all(np.abs(g - c) <= rtol * scale)
+
+
+def solver(p, block=None, dtype="f64", **opt):
+    return J.Solver(p.dims, block or p.block, dtype=dtype, faces=p.faces, source=p.source, x0=p.x0, **opt)
+
+
+# ---- plain FP64 sweeps vs the oracle ---------------------------------------
+
+CASES_2D = [
+    ((256, 256), (64, 64), 100),
+    ((130, 77), (64, 32), 13),       # remainder blocks on both axes
+    ((200, 3), (50, 3), 9),
+    ((1, 1), (1, 1), 5),             # a single point
+    ((1, 40), (1, 7), 6),
+    ((65, 1), (64, 1), 4),           # ragged segment tail
+    ((129, 70), (129, 70), 11),      # monolithic, odd width
+]
+
+CASES_3D = [
+    ((37, 29, 23), (16, 8, 8), 12),
+    ((64, 64, 64), (64, 64, 64), 3),
+    ((20, 6, 9), (7, 5, 2), 7),
+    ((3, 1, 2), (1, 1, 1), 4),
+    ((130, 9, 5), (64, 4, 3), 5),
+]
+
+
+@pytest.mark.parametrize("dims,block,k", CASES_2D + CASES_3D)
+def test_sweeps_match_oracle(dims, block, k):
+    p = inputs.make_problem(dims, block, 41, boundary="uniform", source="normal", x0="uniform")
+    with solver(p) as s:
+        s.sweep(k)
+        got = s.field()
+    ref = oracle.sweeps(p.dims, p.faces, p.source, p.x0, k)
+    assert per_point_close(got, ref)
+    assert np.array_equal(got, ref)  # expected: identical operation order
+
+
+def test_laplace_256_matches_golden_fixture():
+    path = os.path.join(os.path.dirname(__file__), "golden", "laplace_2d_256_100.json")
+    doc = json.load(open(path))
+    p = inputs.laplace_2d_small()
+    with solver(p) as s:
+        s.sweep(doc["sweeps"])
+        x = s.field()
+        rel, ab = s.residual()
+    for y, xx, v in doc["points"]:
+        assert x[y, xx] == float.fromhex(v)
+    rss = float.fromhex(doc["rss"])
+    assert abs(ab * ab - rss) <= 1e-12 * rss
+
+
+# ---- over-decomposition invariance (bit-exact) -----------------------------
+
+@pytest.mark.parametrize("dims,blocks", [
+    ((300, 190), [(300, 190), (64, 64), (100, 37), (7, 190), (300, 1), (33, 50)]),
+    ((40, 33, 27), [(40, 33, 27), (8, 8, 8), (13, 5, 27), (40, 1, 3), (5, 33, 1)]),
+])
+@pytest.mark.parametrize("halo", [0, 1])
+def test_over_decomposition_bit_exact(dims, blocks, halo):
+    p = inputs.make_problem(dims, dims, 43, boundary="uniform", source="normal", x0="uniform")
+    ref = None
+    for b in blocks:
+        with solver(p, block=b, halo=halo) as s:
+            s.sweep(17)
+            x = s.field()
+        if ref is None:
+            ref = x
+        assert np.array_equal(x, ref), b
+
+
+@pytest.mark.parametrize("rows", [1, 3, 64])
+def test_work_item_shape_does_not_change_results(rows):
+    p = inputs.make_problem((150, 140), (64, 70), 44, boundary="uniform", source="normal", x0="uniform")
+    with solver(p) as s:
+        s.sweep(9)
+        ref = s.field()
+    with solver(p, rows_f64=rows) as s:
+        s.sweep(9)
+        assert np.array_equal(s.field(), ref)
+    p3 = inputs.make_problem((70, 20, 30), (64, 10, 16), 45, boundary="uniform", source="normal", x0="uniform")
+    with solver(p3) as s:
+        s.sweep(5)
+        ref3 = s.field()
+    with solver(p3, rows_f64=rows) as s:
+        s.sweep(5)
+        assert np.array_equal(s.field(), ref3)
+
+
+# ---- residual ---------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,block", [((256, 200), (64, 64)), ((70, 40, 30), (64, 16, 8)), ((5, 7), (2, 3))])
+def test_residual_matches_oracle(dims, block):
+    p = inputs.make_problem(dims, block, 46, boundary="uniform", source="normal", x0="uniform")
+    with solver(p) as s:
+        s.sweep(3)
+        x = s.field()
+        rel, ab = s.residual()
+    rss, bss = oracle.residual(p.dims, p.faces, p.source, x)
+    assert abs(ab - np.sqrt(rss)) <= 1e-12 * np.sqrt(rss)
+    assert abs(rel - np.sqrt(rss) / np.sqrt(bss)) <= 1e-12 * rel
+
+
+def test_residual_decomposition_independent():
+    """Residual partials are keyed on global (row, 64-point segment), so any
+    decomposition whose block widths are multiples of 64 gives the same bits."""
+    p = inputs.make_problem((256, 100), (256, 100), 47, boundary="uniform", source="normal", x0="uniform")
+    vals = []
+    for b in [(256, 100), (64, 10), (128, 33), (64, 100)]:
+        with solver(p, block=b) as s:
+            s.sweep(4)
+            vals.append(s.residual())
+    assert all(v == vals[0] for v in vals)
+
+
+# ---- closed forms on the GPU -------------------------------------------------
+
+def test_gpu_eigenmode_decay():
+    from tests.test_oracle_pins import decay_factor, sine_mode
+    for dims, modes, block in [((63, 47), (3, 5), (32, 16)), ((19, 17, 15), (2, 1, 3), (8, 8, 4))]:
+        x0 = sine_mode(dims, modes)
+        lam = decay_factor(dims, modes)
+        with J.Solver(dims, block, x0=x0) as s:
+            s.sweep(20)
+            x = s.field()
+        assert np.max(np.abs(x - lam ** 20 * x0)) <= (4 + 8 * 20) * np.finfo(float).eps
+
+
+def test_gpu_harmonic_fixed_point():
+    from tests.test_oracle_pins import field_and_faces, harmonic_fields
+    for dims, block in [((31, 17), (8, 8)), ((9, 10, 11), (4, 3, 5))]:
+        for u in harmonic_fields(len(dims)):
+            inner, faces = field_and_faces(dims, u)
+            with J.Solver(dims, block, faces=faces, x0=inner) as s:
+                s.sweep(15)
+                assert np.array_equal(s.field(), inner)
+
+
+# ---- solve ---------------------------------------------------------------------
+
+@pytest.mark.parametrize("dims,block", [((48, 40), (16, 16)), ((14, 12, 10), (7, 6, 5))])
+def test_solve_f64_matches_oracle(dims, block):
+    p = inputs.make_problem(dims, block, 48, boundary="uniform", source="normal", x0="zero")
+    st_o, x_o, sw_o, rel_o = oracle.solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, 25)
+    with solver(p, check_every=25) as s:
+        st, sw, rel = s.solve(1e-8, 10 ** 6)
+        x = s.field()
+    assert st == J.OK and st_o == oracle.OK
+    assert sw == sw_o
+    assert np.array_equal(x, x_o)
+    assert abs(rel - rel_o) <= 1e-10 * rel_o
+
+
+def test_solve_cap_and_continue():
+    p = inputs.make_problem((40, 30), (20, 10), 49, boundary="uniform", source="normal", x0="zero")
+    with solver(p, check_every=7) as s:
+        st, sw, rel = s.solve(1e-14, 30)
+        assert st == J.ERR_NOT_CONVERGED and sw == 30
+        x30 = s.field()
+        st, sw, rel = s.solve(1e-14, 5)
+        assert sw == 5
+        x35 = s.field()
+    assert np.array_equal(x30, oracle.sweeps(p.dims, p.faces, p.source, None, 30))
+    assert np.array_equal(x35, oracle.sweeps(p.dims, p.faces, p.source, None, 35))
+
+
+# ---- mixed-precision refinement ---------------------------------------------
+
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False)])
+@pytest.mark.parametrize("dims,block", [((60, 45), (32, 16)), ((16, 14, 12), (8, 7, 6))])
+def test_refine_matches_oracle_emulation(dtype, e16, r16, dims, block):
+    p = inputs.make_problem(dims, block, 50, boundary="uniform", source="normal", x0="zero")
+    period = 20
+    st_o, x_o, sw_o, rel_o = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, period,
+                                                 e_bf16=e16, r_bf16=r16)
+    with solver(p, dtype=dtype, refine_period=period) as s:
+        st, sw, rel = s.solve(1e-8, 10 ** 6)
+        x = s.field()
+    assert st == J.OK and st_o == oracle.OK
+    assert oracle.relative_residual(p.dims, p.faces, p.source, x) <= 1e-8
+    assert sw == sw_o
+    assert np.array_equal(x, x_o)
+
+
+def test_refine_r_bf16_converges():
+    p = inputs.make_problem((50, 40), (25, 20), 51, boundary="uniform", source="normal", x0="zero")
+    with J.Solver(p.dims, p.block, dtype="bf16_refine", faces=p.faces, source=p.source) as s:
+        pass
+    # r_bf16 is fixed at creation; exercised through the oracle emulation pin on the CPU
+    st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, 20,
+                                             e_bf16=True, r_bf16=True)
+    assert st_o == oracle.OK
+
+
+def test_refine_sweep_then_field_is_updated():
+    p = inputs.make_problem((64, 64), (32, 32), 52, boundary="uniform", source="normal", x0="uniform")
+    with solver(p, dtype="f32_refine", refine_period=10) as s:
+        s.sweep(30)
+        x = s.field()
+    xp = oracle.sweeps(p.dims, p.faces, p.source, p.x0, 30)
+    corr = np.max(np.abs(xp - p.x0))
+    assert np.max(np.abs(x - xp)) <= 4 * 30 * 2.0 ** -23 * corr
+
+
+# ---- errors and edge cases ------------------------------------------------------
+
+def test_invalid_arguments():
+    with pytest.raises(J.JacobiError) as e:
+        J.Solver((10, 10), (11, 10))
+    assert e.value.status == J.ERR_INVALID
+    with pytest.raises(J.JacobiError):
+        J.Solver((10, 10, 10, 10), (1, 1, 1, 1))
+    with J.Solver((10, 10), (5, 5)) as s:
+        with pytest.raises(J.JacobiError):
+            s.set_option("check_every", 0)
+        with pytest.raises(J.JacobiError):
+            s.set_option("no_such_option", 1)
+        st = J.load().jacobi_solve(s.h, -1.0, 10, None, None)
+        assert st == J.ERR_INVALID
+        s.sweep(0)
+
+
+def test_set_field_and_source_round_trip():
+    p = inputs.make_problem((90, 70), (32, 32), 53, boundary="uniform", source="normal", x0="uniform")
+    with solver(p) as s:
+        x1 = inputs.uniform(7, 1, 90 * 70).reshape(70, 90)
+        s.set_field(x1)
+        assert np.array_equal(s.field(), x1)
+        f2 = inputs.normal(7, 2, 90 * 70).reshape(70, 90)
+        s.set_source(f2)
+        s.sweep(6)
+        ref = oracle.sweeps(p.dims, p.faces, f2, x1, 6)
+        assert np.array_equal(s.field(), ref)
+        rel, _ = s.residual()
+        assert abs(rel - oracle.relative_residual(p.dims, p.faces, f2, ref)) <= 1e-12 * rel
+
+
+def test_device_field_io():
+    p = inputs.make_problem((64, 48), (32, 16), 54, boundary="uniform", source="normal", x0="uniform")
+    with solver(p) as s:
+        s.sweep(3)
+        out = torch.empty(p.shape, dtype=torch.float64, device="cuda")
+        s.field(out)
+        torch.cuda.synchronize()
+        host = s.field()
+        assert np.array_equal(out.cpu().numpy(), host)
+        s.set_field(out * 2)
+        torch.cuda.synchronize()
+        assert np.array_equal(s.field(), host * 2)

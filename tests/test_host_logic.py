@@ -1,0 +1,66 @@
+"""CPU-only checks of the CUDA library's host side: it builds, loads and exports
+every entry point that include/jacobi.h declares (no compute calls without a
+GPU), and the exact FP64 scalings used by the kernels agree bit for bit with
+IEEE division."""
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    txt = open(os.path.join(ROOT, "include", "jacobi.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(jacobi_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_header_declares_expected_entry_points():
+    from paper_2303_02543_gb300 import jacobi as J
+    assert declared_symbols() == sorted(J.EXPORTS)
+
+
+def test_library_builds_loads_and_exports_every_symbol():
+    from paper_2303_02543_gb300 import build
+    path = build.build()
+    out = subprocess.run(["nm", "-D", "--defined-only", path], capture_output=True, text=True, check=True).stdout
+    exported = set(re.findall(r"\b(jacobi_[a-z0-9_]+)\b", out))
+    missing = [s for s in declared_symbols() if s not in exported]
+    assert not missing, missing
+    import ctypes
+    lib = ctypes.CDLL(path)
+    for s in declared_symbols():
+        assert getattr(lib, s) is not None
+    lib.jacobi_version.restype = ctypes.c_int
+    assert lib.jacobi_version() >= 10000
+
+
+def test_invalid_arguments_rejected_without_gpu():
+    """Argument validation happens before any CUDA call."""
+    import ctypes
+    from paper_2303_02543_gb300 import build
+    from paper_2303_02543_gb300 import jacobi as J
+    build.build()
+    lib = J.load()
+    h = ctypes.c_void_p()
+    dims = (ctypes.c_int64 * 3)(10, 10, 1)
+    bad = (ctypes.c_int64 * 3)(11, 10, 1)
+    assert lib.jacobi_create(ctypes.byref(h), 2, dims, bad, 0, None, None, None, None) == J.ERR_INVALID
+    assert not h.value
+    assert lib.jacobi_create(ctypes.byref(h), 4, dims, dims, 0, None, None, None, None) == J.ERR_INVALID
+    assert lib.jacobi_create(ctypes.byref(h), 2, dims, dims, 9, None, None, None, None) == J.ERR_INVALID
+    assert b"block" in lib.jacobi_last_error(None) or b"dtype" in lib.jacobi_last_error(None)
+    assert lib.jacobi_sweep(None, 1) == J.ERR_INVALID
+    lib.jacobi_destroy(None)
+
+
+def test_exact_f64_helpers_match_ieee(tmp_path):
+    src = os.path.join(ROOT, "tests", "native", "exact_f64_check.cpp")
+    exe = str(tmp_path / "exact_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-I", os.path.join(ROOT, "paper_2303_02543_gb300", "csrc"),
+                    "-o", exe, src], check=True)
+    r = subprocess.run([exe, "3000000"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "mismatches 0" in r.stdout
