@@ -91,11 +91,18 @@ def load(path: str | None = None):
 
 
 def use_torch_allocator(enable: bool = True):
-    """Route the library's device allocations through torch's caching allocator."""
+    """Route the library's device allocations through torch's caching allocator.
+
+    The ctypes trampolines are created once and kept for the life of the
+    process: a context keeps the hooks it was created with, so replacing them
+    while a context is alive would leave it calling freed code."""
     global _alloc_cb, _free_cb
     lib = load()
     if not enable:
         lib.jacobi_set_allocator(ALLOC_FN(), FREE_FN(), None)
+        return
+    if _alloc_cb is not None:
+        lib.jacobi_set_allocator(_alloc_cb, _free_cb, None)
         return
     import torch
 

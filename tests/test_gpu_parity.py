@@ -276,3 +276,21 @@ def test_device_field_io():
         s.set_field(out * 2)
         torch.cuda.synchronize()
         assert np.array_equal(s.field(), host * 2)
+
+
+def test_two_live_solvers_share_allocator_hooks():
+    """Creating a second context must leave the first one usable (the
+    allocator hooks a context captured stay valid)."""
+    p = inputs.make_problem((64, 40), (32, 20), 55, boundary="uniform", source="normal", x0="uniform")
+    a = solver(p)
+    b = solver(p, dtype="f32_refine")
+    c = solver(p, dtype="bf16_refine")
+    a.sweep(4)
+    a.set_field(p.x0)
+    a.sweep(4)
+    xa = a.field()
+    b.sweep(4)
+    c.sweep(4)
+    for s in (c, b, a):
+        s.close()
+    assert np.array_equal(xa, oracle.sweeps(p.dims, p.faces, p.source, p.x0, 4))

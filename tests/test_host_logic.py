@@ -64,3 +64,18 @@ def test_exact_f64_helpers_match_ieee(tmp_path):
     r = subprocess.run([exe, "3000000"], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "mismatches 0" in r.stdout
+
+
+def test_torch_allocator_trampolines_are_created_once():
+    """A context keeps the allocator hooks it was created with; reinstalling
+    must not free the ctypes trampolines those hooks point to."""
+    pytest.importorskip("torch")
+    from paper_2303_02543_gb300 import build
+    from paper_2303_02543_gb300 import jacobi as J
+    build.build()
+    J.use_torch_allocator(True)
+    a, f = J._alloc_cb, J._free_cb
+    J.use_torch_allocator(True)
+    J.use_torch_allocator(False)
+    J.use_torch_allocator(True)
+    assert J._alloc_cb is a and J._free_cb is f
