@@ -55,7 +55,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poisson2d_8192",
-                    choices=["poisson2d_8192", "laplace2d_256", "poisson3d_512"])
+                    choices=["poisson2d_8192", "poisson2d_4096", "laplace2d_256", "poisson3d_512", "poisson3d_256"])
+    ap.add_argument("--sweeps", type=int, default=0, help="override the sweeps per step (profiling runs)")
     ap.add_argument("--forms", default="f64,f32_refine,bf16_refine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -76,6 +77,12 @@ def make_workload(name):
     if name == "poisson2d_8192":
         p = inputs.poisson_2d_large()
         desc = "2D 5-point Poisson 8192x8192 FP64, 16x16 blocks of 512x512, 1000 sweeps, residual every 50"
+    elif name == "poisson2d_4096":
+        p = inputs.poisson_2d_large(n=4096)
+        desc = "2D 5-point Poisson 4096x4096 FP64, 8x8 blocks of 512x512 (profiling size, > L2)"
+    elif name == "poisson3d_256":
+        p = inputs.poisson_3d(n=256)
+        desc = "3D 7-point Poisson 256^3 FP64, blocks of 64^3 (profiling size, > L2)"
     elif name == "laplace2d_256":
         p = inputs.laplace_2d_small()
         desc = "2D 5-point Laplace 256x256 FP64, 4x4 blocks of 64x64, 100 sweeps"
@@ -176,7 +183,8 @@ def oracle_sample(p, sweeps):
 
 
 def cpu_baseline(p, name):
-    sweeps = {"poisson2d_8192": 50, "laplace2d_256": 2000, "poisson3d_512": 20}[name]
+    sweeps = {"poisson2d_8192": 50, "poisson2d_4096": 200, "laplace2d_256": 2000, "poisson3d_512": 20,
+              "poisson3d_256": 100}[name]
     glups, dt, cores = oracle_sample(p, sweeps)
     return {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
             "sample": f"{sweeps} sweeps of the full {'x'.join(map(str, p.dims))} grid with residual tests "
@@ -187,7 +195,8 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     p, desc, _ = make_workload(args.workload)
-    sweeps = {"poisson2d_8192": 5, "laplace2d_256": 500, "poisson3d_512": 2}[args.workload]
+    sweeps = {"poisson2d_8192": 5, "poisson2d_4096": 20, "laplace2d_256": 500, "poisson3d_512": 2,
+              "poisson3d_256": 10}[args.workload]
     for _ in range(args.warmup):
         oracle_sample(p, sweeps)
     t0 = time.perf_counter()
@@ -284,6 +293,8 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     p, desc, sweeps = make_workload(args.workload)
+    if args.sweeps > 0:
+        sweeps = args.sweeps
     hbm_peak, peak_kind = measured_peaks()
     forms = [f for f in args.forms.split(",") if f]
     results = {}
