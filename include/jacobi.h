@@ -165,6 +165,37 @@ const char* jacobi_last_error(jacobi_t ctx);
 /* Library version: major * 10000 + minor * 100 + patch. */
 int jacobi_version(void);
 
+/* Residual of an interior-dense field WITHOUT ANY DEVICE ALLOCATION.
+ *
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot call cudaMalloc -- a process whose device memory is owned in full by
+ * another runtime's pool, or a latency-bound loop that must never stall the
+ * device, since cudaMalloc and cudaFree may synchronise it.  It computes
+ * *rss_out = sum over the grid of r_p^2 with r = b - A x, the same fused
+ * residual and deterministic reduction as jacobi_residual, and its value is
+ * bit-identical to that of a monolithic context holding the same field.
+ *
+ *   ndim, dims  as in jacobi_create.
+ *   x           device, interior-dense FP64 field (read).
+ *   f           device, interior-dense FP64 source, or NULL for f = 0.
+ *   faces       NULL, or 2*ndim device pointers (entries may be NULL for a zero
+ *               face) laid out as in jacobi_boundary.
+ *   rss_out     device pointer to one double (written).
+ *   cuda_stream the stream the two kernels run on (NULL: legacy stream);
+ *               the call returns without synchronising.
+ *
+ * Scratch: one fixed array in device global memory (a file-scope __device__
+ * variable of about 8 MiB that every GPU which loads the library keeps until
+ * the process exits).  The grid must satisfy ny * nz * ceil(nx / 64) <= 2^20
+ * (8192 x 8192 fits; 512^3 does not); larger grids return JACOBI_ERR_INVALID
+ * before any GPU work.  The first call on a device looks up the array's
+ * device address with that device current; make that first call before any
+ * stream capture.  Every call shares the array, so calls that overlap on the
+ * GPU (on different streams, or from different threads) race: order them.
+ * Errors are reported through jacobi_last_error(NULL). */
+jacobi_status jacobi_residual_noalloc(int ndim, const int64_t dims[3], const double* x, const double* f,
+                                      const double* const faces[6], double* rss_out, void* cuda_stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -17,6 +17,11 @@ struct jacobi_ctx {
 
 static thread_local std::string t_err;
 
+namespace jgb {
+// Records the calling thread's last error for entry points without a context.
+void set_thread_error(const std::string& msg) { t_err = msg; }
+}  // namespace jgb
+
 #define API_BEGIN try {
 #define API_END(ctx)                                              \
   }                                                               \

@@ -29,7 +29,7 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT
 EXPORTS = ["jacobi_set_allocator", "jacobi_create", "jacobi_sweep", "jacobi_residual", "jacobi_solve",
            "jacobi_get_field", "jacobi_set_field", "jacobi_set_source", "jacobi_set_option",
            "jacobi_get_option", "jacobi_profile", "jacobi_device_bytes", "jacobi_destroy",
-           "jacobi_last_error", "jacobi_version"]
+           "jacobi_last_error", "jacobi_version", "jacobi_residual_noalloc"]
 
 
 class JacobiError(RuntimeError):
@@ -81,6 +81,7 @@ def load(path: str | None = None):
         "jacobi_destroy": (None, [vp]),
         "jacobi_last_error": (ctypes.c_char_p, [vp]),
         "jacobi_version": (ctypes.c_int, []),
+        "jacobi_residual_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, vp, vp, ctypes.POINTER(vp), vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -220,6 +221,17 @@ def jacobi_device_bytes(h):
 def jacobi_destroy(h):
     if h:
         load().jacobi_destroy(h)
+
+
+def jacobi_residual_noalloc(ndim, dims, x_ptr, f_ptr, face_ptrs, rss_ptr, stream=None):
+    """Residual sum of squares of an interior-dense device field into the
+    device double at rss_ptr, using only the library's fixed scratch."""
+    dl = list(dims)[:3]
+    d = (ctypes.c_int64 * 3)(*(dl + [1] * (3 - len(dl))))
+    fp = None
+    if face_ptrs is not None:
+        fp = (ctypes.c_void_p * 6)(*(list(face_ptrs) + [None] * (6 - len(face_ptrs))))
+    return _check(load().jacobi_residual_noalloc(int(ndim), d, x_ptr, f_ptr, fp, rss_ptr, stream), None)
 
 
 def jacobi_last_error(h=None):
