@@ -61,14 +61,20 @@ typedef enum {
   JACOBI_ERR_BUSY = 7            /* server: request pending or cannot be admitted */
 } jacobi_status;
 
-/* Arithmetic of the iteration.
- *   JACOBI_F64          plain FP64 Jacobi sweeps.
- *   JACOBI_F32_REFINE   iterative refinement: r = b - A x and x += e in FP64,
- *                       inner Jacobi sweeps of A e = r (zero boundary) in FP32.
- *   JACOBI_BF16_REFINE  as F32_REFINE with e stored as bfloat16 (RNE) and the
- *                       inner sweeps computed in FP32; r stored as FP32 (or
- *                       bfloat16 with option "r_bf16" = 1). */
-typedef enum { JACOBI_F64 = 0, JACOBI_F32_REFINE = 1, JACOBI_BF16_REFINE = 2 } jacobi_dtype;
+/* Arithmetic of the iteration (the paper fixes none; FP64 is the plain form).
+ *   JACOBI_F64              plain FP64 Jacobi sweeps.
+ *   JACOBI_F32_REFINE       iterative refinement: r = b - A x and x += e in
+ *                           FP64, inner Jacobi sweeps of A e = r (zero
+ *                           boundary, e starting at 0) in FP32.
+ *   JACOBI_BF16_REFINE      as F32_REFINE with e stored as bfloat16 (RNE),
+ *                           inner sweeps computed in FP32, r stored as FP32.
+ *   JACOBI_BF16_REFINE_R16  as BF16_REFINE with r also stored as bfloat16. */
+typedef enum {
+  JACOBI_F64 = 0,
+  JACOBI_F32_REFINE = 1,
+  JACOBI_BF16_REFINE = 2,
+  JACOBI_BF16_REFINE_R16 = 3
+} jacobi_dtype;
 
 typedef enum { JACOBI_BC_ZERO = 0, JACOBI_BC_CONST = 1, JACOBI_BC_FACES = 2 } jacobi_bc_kind;
 
@@ -133,13 +139,28 @@ jacobi_status jacobi_set_field(jacobi_t ctx, const double* in, int on_device);
 /* Replace the source term f (interior-dense, host or device memory). */
 jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
 
-/* Integer options:
- *   "check_every"    sweeps between residual tests in jacobi_solve (F64), >= 1
- *   "refine_period"  inner sweeps per outer refinement step, >= 1
- *   "halo"           0 = fused into the sweep (default), 1 = separate pack/unpack kernels
- *   "rows_f64"       lines per warp work item of the FP64 kernels (>= 1)
- *   "rows_low"       lines per warp work item of the low-precision kernels (>= 1)
- *   "r_bf16"         BF16_REFINE only: store r as bfloat16 (0/1)
+/* Integer options (none changes a result bit; they choose how the work runs):
+ *   "check_every"    sweeps between residual tests in jacobi_solve (F64), >= 1 (default 50)
+ *   "refine_period"  inner sweeps per outer refinement step, 1..4096 (default 20)
+ *   "halo"           0 = halo exchange fused into the sweep (default),
+ *                    1 = separate pack and unpack kernels after every sweep
+ *                    (section 4.3's pack / transfer / unpack steps)
+ *   "rows_f64"       lines per warp work item of the FP64 kernels (default 32)
+ *   "rows_low"       lines per warp work item of the low-precision kernels (default 32)
+ *   "schedule"       0 = one launch per sweep (default); 1 = persistent block
+ *                    scheduler: one launch runs many sweeps, blocks wait for
+ *                    their neighbours' previous sweep, never for a global
+ *                    barrier (section 3.1.4's scheduler with section 3.1.2's
+ *                    dependencies, on the device).  Needs "halo" = 0.
+ *   "graph"          1: every solve step (inner sweeps + outer step, or a
+ *                    checked chunk of FP64 sweeps) is captured once as a CUDA
+ *                    graph and replayed (section 3.1.3's explicit task graph)
+ *   "spin_limit"     iterations a persistent-scheduler wait may spin before it
+ *                    gives up with JACOBI_ERR_TIMEOUT (default 2^22)
+ *   "poison_wait"    test hook: 1 makes every persistent-scheduler wait run out
+ *   "autotune"       1: before the first solve, time the candidate work-item
+ *                    shapes and schedules and keep the fastest (cached in the
+ *                    file named by the environment variable JACOBI_TUNE_CACHE)
  *   "profile"        1: time every kernel launch with CUDA events (see jacobi_profile) */
 jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value);
 jacobi_status jacobi_get_option(jacobi_t ctx, const char* key, int64_t* value);
@@ -149,7 +170,7 @@ jacobi_status jacobi_get_option(jacobi_t ctx, const char* key, int64_t* value);
  * "refine_outer", "reduce", "halo").  Synchronises the stream.  reset = 1
  * clears the counters afterwards.  kernel = "all" reports, in *launches, every
  * kernel launch the context has issued since creation (profiling not needed)
- * and 0 in *total_ms. */
+ * and 0 in *total_ms; kernel = "graph" reports the CUDA graph replays. */
 jacobi_status jacobi_profile(jacobi_t ctx, const char* kernel, double* total_ms, int64_t* launches, int reset);
 
 /* Bytes of device memory held by the context. */
@@ -164,6 +185,45 @@ const char* jacobi_last_error(jacobi_t ctx);
 
 /* Library version: major * 10000 + minor * 100 + patch. */
 int jacobi_version(void);
+
+/* ---- batches: many independent grids in every launch -------------------- */
+
+/* One problem of a batch (host memory; see jacobi_create). */
+typedef struct {
+  int ndim;
+  int64_t dims[3];
+  int64_t block[3];
+  jacobi_boundary bc;
+  const double* source; /* NULL: f = 0 */
+  const double* x0;     /* NULL: 0 */
+} jacobi_problem;
+
+/* Outcome of one problem. */
+typedef struct {
+  int32_t status;   /* JACOBI_OK, JACOBI_ERR_NOT_CONVERGED or JACOBI_ERR_DIVERGED */
+  int32_t reserved;
+  int64_t sweeps;   /* sweeps (inner sweeps for refinement) at the accepted iterate */
+  double rel;       /* relative residual of the returned field */
+  double seconds;   /* wall time from the start of the batch solve to this decision */
+} jacobi_result;
+
+/* Create one context holding n independent grids of the same ndim (section
+ * 4.4's over-decomposition across problems: every block of every grid is a
+ * work item of the same launches).  Each grid's arithmetic does not depend on
+ * the others: its field and sweep count equal those of solving it alone.
+ * Options, jacobi_sweep (all grids), jacobi_profile, jacobi_device_bytes,
+ * jacobi_destroy and jacobi_last_error apply to batch contexts; the other
+ * single-grid calls return JACOBI_ERR_INVALID on them. */
+jacobi_status jacobi_batch_create(jacobi_t* out, int n, const jacobi_problem* probs, int dtype, void* cuda_stream);
+
+/* Solve every grid to its relative residual <= tol (the rule of jacobi_solve,
+ * all grids stepping together; a grid retires as soon as it passes).
+ * results[i] (may be NULL) receives grid i's outcome.  Returns JACOBI_OK when
+ * every grid converged, else the first non-OK status. */
+jacobi_status jacobi_batch_solve(jacobi_t ctx, double tol, int64_t max_sweeps, jacobi_result* results);
+
+/* Copy grid i's current iterate out (interior-dense, host or device memory). */
+jacobi_status jacobi_batch_get_field(jacobi_t ctx, int i, double* out, int on_device);
 
 /* Residual of an interior-dense field WITHOUT ANY DEVICE ALLOCATION.
  *

@@ -45,81 +45,10 @@ static void require(bool ok, const std::string& msg) {
   if (!ok) throw JErr{JACOBI_ERR_INVALID, msg};
 }
 
-// ---------------------------------------------------------------------------
-// solve loops shared by the single-grid context
-
 static double rel_of(double rss, double bss) { return bss > 0.0 ? std::sqrt(rss) / std::sqrt(bss) : std::sqrt(rss); }
 
-// Plain FP64: the residual of iterate m is reduced inside sweep m+1 (the
-// last sweep of a chunk); when the test passes, the phase flips back so the
-// field is iterate m again.  One extra sweep is run and discarded.
-static jacobi_status solve_f64(Workset& ws, int slot, double tol, int64_t max_sweeps, int64_t* done, double* rel_out) {
-  SolveHost* s = ws.solve(slot);
-  const int64_t c = ws.opt.check_every;
-  std::vector<double> rss;
-  int64_t m = 0;
-  ws.sweeps_f64(1, true);
-  jacobi_status st;
-  double rel;
-  for (;;) {
-    ws.read_rss(rss);
-    rel = rel_of(rss[slot], s->bss);
-    if (!std::isfinite(rel)) {
-      st = JACOBI_ERR_DIVERGED;
-      break;
-    }
-    if (rel <= tol) {
-      st = JACOBI_OK;
-      break;
-    }
-    if (m >= max_sweeps) {
-      st = JACOBI_ERR_NOT_CONVERGED;
-      break;
-    }
-    const int64_t n = std::min(c, max_sweeps - m);
-    ws.sweeps_f64(n, true);
-    m += n;
-  }
-  ws.phase_advance(1, -1);  // back to iterate m
-  if (done) *done = m;
-  if (rel_out) *rel_out = rel;
-  return st;
-}
-
-// Refinement: outer step (x += e, r = b - A x in FP64, residual), then
-// refine_period inner sweeps; the test follows every outer step.
-static jacobi_status solve_refine(Workset& ws, int slot, double tol, int64_t max_sweeps, int64_t* done,
-                                  double* rel_out) {
-  SolveHost* s = ws.solve(slot);
-  const int64_t k = ws.opt.refine_period;
-  std::vector<double> rss;
-  int64_t m = 0;
-  jacobi_status st;
-  double rel;
-  for (;;) {
-    ws.refine_outer();
-    ws.read_rss(rss);
-    rel = rel_of(rss[slot], s->bss);
-    if (!std::isfinite(rel)) {
-      st = JACOBI_ERR_DIVERGED;
-      break;
-    }
-    if (rel <= tol) {
-      st = JACOBI_OK;
-      break;
-    }
-    if (m >= max_sweeps) {
-      st = JACOBI_ERR_NOT_CONVERGED;
-      break;
-    }
-    const int64_t n = std::min(k, max_sweeps - m);
-    ws.refine_inner(n);
-    m += n;
-  }
-  ws.phase_advance(0, 0);  // the correction has been applied
-  if (done) *done = m;
-  if (rel_out) *rel_out = rel;
-  return st;
+static void require_single(jacobi_ctx* ctx) {
+  require(ctx->ws->live() == 1, "this call needs a single-grid context; use the jacobi_batch_* calls");
 }
 
 // ---------------------------------------------------------------------------
@@ -168,7 +97,7 @@ jacobi_status jacobi_create(jacobi_t* out, int ndim, const int64_t dims[3], cons
   API_BEGIN
   require(out != nullptr, "out is NULL");
   *out = nullptr;
-  require(dtype >= 0 && dtype <= 2, "unknown dtype");
+  require(dtype >= 0 && dtype <= 3, "unknown dtype");
   ProblemSpec p;
   fill_spec(p, ndim, dims, block, bc, source, x0);
   ctx = new jacobi_ctx();
@@ -211,6 +140,7 @@ jacobi_status jacobi_sweep(jacobi_t ctx, int64_t n) {
 jacobi_status jacobi_residual(jacobi_t ctx, double* rel, double* abs) {
   if (!ctx) return JACOBI_ERR_INVALID;
   API_BEGIN
+  require_single(ctx);
   Workset& ws = *ctx->ws;
   ws.residual_only();
   std::vector<double> rss;
@@ -227,9 +157,13 @@ jacobi_status jacobi_solve(jacobi_t ctx, double tol, int64_t max_sweeps, int64_t
   API_BEGIN
   require(tol > 0.0, "tol must be > 0");
   require(max_sweeps >= 0, "max_sweeps must be >= 0");
-  Workset& ws = *ctx->ws;
-  return ws.refine() ? solve_refine(ws, ctx->slot, tol, max_sweeps, sweeps_done, final_rel)
-                     : solve_f64(ws, ctx->slot, tol, max_sweeps, sweeps_done, final_rel);
+  require_single(ctx);
+  std::vector<SlotResult> res;
+  ctx->ws->solve_all(tol, max_sweeps, res);
+  const SlotResult& r = res[ctx->slot];
+  if (sweeps_done) *sweeps_done = r.sweeps;
+  if (final_rel) *final_rel = r.rel;
+  return (jacobi_status)r.status;
   API_END(ctx)
 }
 
@@ -237,6 +171,7 @@ jacobi_status jacobi_get_field(jacobi_t ctx, double* out, int on_device) {
   if (!ctx) return JACOBI_ERR_INVALID;
   API_BEGIN
   require(out != nullptr, "out is NULL");
+  require_single(ctx);
   ctx->ws->gather(ctx->slot, out, on_device);
   return JACOBI_OK;
   API_END(ctx)
@@ -246,6 +181,7 @@ jacobi_status jacobi_set_field(jacobi_t ctx, const double* in, int on_device) {
   if (!ctx) return JACOBI_ERR_INVALID;
   API_BEGIN
   require(in != nullptr, "in is NULL");
+  require_single(ctx);
   Workset& ws = *ctx->ws;
   ws.scatter(ctx->slot, in, 0, on_device);
   ws.halo_exchange_x(0);
@@ -258,6 +194,7 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device) {
   if (!ctx) return JACOBI_ERR_INVALID;
   API_BEGIN
   require(in != nullptr, "in is NULL");
+  require_single(ctx);
   Workset& ws = *ctx->ws;
   SolveHost* s = ws.solve(ctx->slot);
   ws.scatter(ctx->slot, in, 1, on_device);
@@ -285,8 +222,12 @@ static int64_t* option_slot(Options& o, const char* key) {
   if (!strcmp(key, "halo")) return &o.halo;
   if (!strcmp(key, "rows_f64")) return &o.rows_f64;
   if (!strcmp(key, "rows_low")) return &o.rows_low;
-  if (!strcmp(key, "r_bf16")) return &o.r_bf16;
   if (!strcmp(key, "profile")) return &o.profile;
+  if (!strcmp(key, "schedule")) return &o.schedule;
+  if (!strcmp(key, "graph")) return &o.graph;
+  if (!strcmp(key, "spin_limit")) return &o.spin_limit;
+  if (!strcmp(key, "poison_wait")) return &o.poison_wait;
+  if (!strcmp(key, "autotune")) return &o.autotune;
   return nullptr;
 }
 
@@ -296,12 +237,13 @@ jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value) {
   Workset& ws = *ctx->ws;
   int64_t* p = option_slot(ws.opt, key);
   require(p != nullptr, std::string("unknown option ") + (key ? key : "(null)"));
-  if (!strcmp(key, "check_every") || !strcmp(key, "refine_period") || !strcmp(key, "rows_f64") ||
-      !strcmp(key, "rows_low"))
-    require(value >= 1, std::string(key) + " must be >= 1");
-  if (!strcmp(key, "halo") || !strcmp(key, "profile")) require(value == 0 || value == 1, std::string(key) + " must be 0 or 1");
-  if (!strcmp(key, "r_bf16")) require(false, "r_bf16 is fixed when the context is created");
-  const bool retable = (!strcmp(key, "rows_f64") || !strcmp(key, "rows_low")) && *p != value;
+  const std::string k(key);
+  if (k == "check_every" || k == "rows_f64" || k == "rows_low") require(value >= 1, k + " must be >= 1");
+  if (k == "refine_period") require(value >= 1 && value <= 4096, "refine_period must be in [1, 4096]");
+  if (k == "halo" || k == "profile" || k == "schedule" || k == "graph" || k == "poison_wait" || k == "autotune")
+    require(value == 0 || value == 1, k + " must be 0 or 1");
+  if (k == "spin_limit") require(value >= 0 && value <= 0x7fffffff, "spin_limit must be in [0, 2^31)");
+  const bool retable = (k == "rows_f64" || k == "rows_low") && *p != value;
   *p = value;
   if (retable) ws.rebuild_tables();
   return JACOBI_OK;
@@ -328,6 +270,12 @@ jacobi_status jacobi_profile(jacobi_t ctx, const char* kernel, double* total_ms,
   else if (!strcmp(kernel, "refine_outer")) k = kProfOuter;
   else if (!strcmp(kernel, "reduce")) k = kProfReduce;
   else if (!strcmp(kernel, "halo")) k = kProfHalo;
+  if (!strcmp(kernel, "graph")) {
+    ctx->ws->sync();
+    if (total_ms) *total_ms = 0.0;
+    if (launches) *launches = ctx->ws->graph_replays();
+    return JACOBI_OK;
+  }
   if (!strcmp(kernel, "all")) {  // every kernel launched by this context so far
     ctx->ws->sync();
     if (total_ms) *total_ms = 0.0;
@@ -356,5 +304,66 @@ void jacobi_destroy(jacobi_t ctx) {
 }
 
 const char* jacobi_last_error(jacobi_t ctx) { return ctx ? ctx->err.c_str() : t_err.c_str(); }
+
+jacobi_status jacobi_batch_create(jacobi_t* out, int n, const jacobi_problem* probs, int dtype, void* cuda_stream) {
+  jacobi_ctx* ctx = nullptr;
+  API_BEGIN
+  require(out != nullptr, "out is NULL");
+  *out = nullptr;
+  require(n >= 1 && n <= (1 << 20), "n must be in [1, 2^20]");
+  require(probs != nullptr, "probs is NULL");
+  require(dtype >= 0 && dtype <= 3, "unknown dtype");
+  std::vector<ProblemSpec> specs((size_t)n);
+  for (int i = 0; i < n; ++i) {
+    fill_spec(specs[i], probs[i].ndim, probs[i].dims, probs[i].block, &probs[i].bc, probs[i].source, probs[i].x0);
+    require(specs[i].ndim == specs[0].ndim, "every problem of a batch must have the same ndim");
+  }
+  ctx = new jacobi_ctx();
+  try {
+    ctx->ws = new Workset(specs[0].ndim, dtype, (cudaStream_t)cuda_stream, n);
+    for (int i = 0; i < n; ++i) ctx->ws->add_solve(specs[i]);
+  } catch (...) {
+    delete ctx->ws;
+    delete ctx;
+    ctx = nullptr;
+    throw;
+  }
+  *out = ctx;
+  return JACOBI_OK;
+  API_END(ctx)
+}
+
+jacobi_status jacobi_batch_solve(jacobi_t ctx, double tol, int64_t max_sweeps, jacobi_result* results) {
+  if (!ctx) return JACOBI_ERR_INVALID;
+  API_BEGIN
+  require(tol > 0.0, "tol must be > 0");
+  require(max_sweeps >= 0, "max_sweeps must be >= 0");
+  std::vector<SlotResult> res;
+  ctx->ws->solve_all(tol, max_sweeps, res);
+  jacobi_status worst = JACOBI_OK;
+  for (int i = 0; i < ctx->ws->capacity(); ++i) {
+    if (!ctx->ws->solve(i)) continue;
+    if (results) {
+      results[i].status = res[i].status;
+      results[i].reserved = 0;
+      results[i].sweeps = res[i].sweeps;
+      results[i].rel = res[i].rel;
+      results[i].seconds = res[i].seconds;
+    }
+    if (res[i].status != JACOBI_OK && worst == JACOBI_OK) worst = (jacobi_status)res[i].status;
+  }
+  return worst;
+  API_END(ctx)
+}
+
+jacobi_status jacobi_batch_get_field(jacobi_t ctx, int i, double* out, int on_device) {
+  if (!ctx) return JACOBI_ERR_INVALID;
+  API_BEGIN
+  require(out != nullptr, "out is NULL");
+  require(ctx->ws->solve(i) != nullptr, "no such problem index");
+  ctx->ws->gather(i, out, on_device);
+  return JACOBI_OK;
+  API_END(ctx)
+}
 
 }  // extern "C"

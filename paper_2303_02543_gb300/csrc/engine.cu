@@ -1,10 +1,15 @@
 // Host engine of the GB300 Jacobi library: block layout, work tables, launch
-// sequences.  See engine.h.
+// sequences, solve loops, CUDA graphs and the autotuner.  See engine.h.
 #include "engine.h"
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 
 namespace jgb {
 
@@ -77,39 +82,17 @@ void DevPool::release(void* p) {
 }
 
 // ---------------------------------------------------------------------------
-// workset
+// layout (section 4.4: the domain cut into blocks, each with a ghost ring)
 
 static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
-Workset::Workset(int ndim, int dtype, cudaStream_t stream, int capacity)
-    : ndim_(ndim), dtype_(dtype), capacity_(capacity), stream_(stream), pool_(current_alloc_hooks(), stream) {
-  solves_.assign(capacity, nullptr);
-  d_solves_ = (SolveDev*)pool_.alloc(sizeof(SolveDev) * capacity);
-  d_rss_ = (double*)pool_.alloc(sizeof(double) * capacity);
-  d_ticket_ = (uint32_t*)pool_.alloc(sizeof(uint32_t) * capacity);
-  cuda_check(cudaMallocHost((void**)&h_rss_, sizeof(double) * capacity), "cudaMallocHost");
-}
-
-Workset::~Workset() {
-  cudaStreamSynchronize(stream_);
-  for (auto* s : solves_) delete s;
-  for (int k = 0; k < kProfCount; ++k)
-    for (auto& p : ev_pending_[k]) {
-      cudaEventDestroy(p.a);
-      cudaEventDestroy(p.b);
-    }
-  for (auto e : ev_free_) cudaEventDestroy(e);
-  if (ev_open_) cudaEventDestroy(ev_open_);
-  if (h_rss_) cudaFreeHost(h_rss_);
-}
-
-void Workset::layout_solve(SolveHost& s) {
+static void layout(SolveHost& s) {
   const ProblemSpec& p = s.spec;
   const int nd = p.ndim;
   for (int a = 0; a < 3; ++a) s.nb[a] = a < nd ? (int)((p.n[a] + p.blk[a] - 1) / p.blk[a]) : 1;
   const int gz = nd == 3 ? 1 : 0;
   int64_t cursor = 0, fcursor = 0;
-  // residual partial layout: segments of every block column, row by row
+  // residual partials: segments of every block column, grid row by grid row
   std::vector<int64_t> seg_base(s.nb[0] + 1, 0);
   for (int i = 0; i < s.nb[0]; ++i) {
     const int64_t bx = i < s.nb[0] - 1 ? p.blk[0] : p.n[0] - (int64_t)(s.nb[0] - 1) * p.blk[0];
@@ -161,6 +144,61 @@ void Workset::layout_solve(SolveHost& s) {
   s.face_elems = round_up(std::max<int64_t>(fcursor, 1), 32);
 }
 
+int64_t solve_device_bytes(const ProblemSpec& p, int dtype, bool r_bf16) {
+  SolveHost s;
+  s.spec = p;
+  layout(s);
+  const int64_t le = dtype >= 2 ? 2 : 4, re = (dtype == 3 || (dtype == 2 && r_bf16)) ? 2 : 4;
+  int64_t b = s.elems * 24 + s.face_elems * 8 + s.nparts * 8 + std::max(1, s.nchunks) * 8;
+  if (dtype != 0) b += s.elems * (2 * le + re) + s.face_elems * le;
+  // work tables: about one 16-byte item per 32 points, plus block descriptors
+  b += (s.points() / 32 + 1) * 16 * (dtype != 0 ? 2 : 1) + (int64_t)s.blocks.size() * 256;
+  return b;
+}
+
+// ---------------------------------------------------------------------------
+// workset
+
+Workset::Workset(int ndim, int dtype, cudaStream_t stream, int capacity, bool r_bf16)
+    : ndim_(ndim), dtype_(dtype), capacity_(capacity), r_bf16_(r_bf16 || dtype == 3), stream_(stream),
+      cur_(stream), pool_(current_alloc_hooks(), stream) {
+  solves_.assign(capacity, nullptr);
+  d_solves_ = (SolveDev*)pool_.alloc(sizeof(SolveDev) * capacity);
+  d_rss_ = (double*)pool_.alloc(sizeof(double) * capacity);
+  d_ticket_ = (uint32_t*)pool_.alloc(sizeof(uint32_t) * capacity);
+  d_ctl_ = (SchedCtl*)pool_.alloc(sizeof(SchedCtl));
+  d_slotctl_ = (int32_t*)pool_.alloc(sizeof(int32_t) * capacity);
+  cuda_check(cudaMallocHost((void**)&h_rss_, sizeof(double) * capacity), "cudaMallocHost");
+  cuda_check(cudaMallocHost((void**)&h_ctl_, sizeof(SchedCtl)), "cudaMallocHost");
+  cuda_check(cudaMallocHost((void**)&h_slotctl_, sizeof(int32_t) * capacity), "cudaMallocHost");
+  cuda_check(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking), "cudaStreamCreate");
+}
+
+Workset::~Workset() {
+  cudaStreamSynchronize(stream_);
+  drop_graphs();
+  for (auto* s : solves_) delete s;
+  for (int k = 0; k < kProfCount; ++k)
+    for (auto& p : ev_pending_[k]) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+  for (auto e : ev_free_) cudaEventDestroy(e);
+  if (ev_open_) cudaEventDestroy(ev_open_);
+  if (h_rss_) cudaFreeHost(h_rss_);
+  if (h_ctl_) cudaFreeHost(h_ctl_);
+  if (h_slotctl_) cudaFreeHost(h_slotctl_);
+  if (cap_stream_) cudaStreamDestroy(cap_stream_);
+}
+
+int Workset::live() const {
+  int n = 0;
+  for (auto* s : solves_) n += s != nullptr;
+  return n;
+}
+
+void Workset::layout_solve(SolveHost& s) { layout(s); }
+
 void Workset::alloc_solve(SolveHost& s) {
   auto a = [&](size_t bytes) {
     void* p = pool_.alloc(bytes);
@@ -172,8 +210,8 @@ void Workset::alloc_solve(SolveHost& s) {
   s.x[1] = (double*)a(E * 8);
   s.f = (double*)a(E * 8);
   if (refine()) {
-    const size_t le = dtype_ == 2 ? 2 : 4;
-    const size_t re = (dtype_ == 2 && opt.r_bf16) ? 2 : 4;
+    const size_t le = dtype_ >= 2 ? 2 : 4;
+    const size_t re = r_bf16_ ? 2 : 4;
     s.e[0] = a(E * le);
     s.e[1] = a(E * le);
     s.r = a(E * re);
@@ -207,7 +245,7 @@ void Workset::push_solve_dev(SolveHost& s) {
   d.active = s.active;
   d.apply_e = s.apply_e;
   d.low = low();
-  d.r_bf16 = (dtype_ == 2 && opt.r_bf16) ? 1 : 0;
+  d.r_bf16 = r_bf16_ ? 1 : 0;
   cuda_check(cudaMemcpyAsync(d_solves_ + s.slot, &d, sizeof(d), cudaMemcpyHostToDevice, stream_), "upload solve");
   cuda_check(cudaStreamSynchronize(stream_), "sync");
 }
@@ -223,16 +261,45 @@ void Workset::set_active(int slot, int active) {
   cuda_check(cudaStreamSynchronize(stream_), "sync");
 }
 
+// Per-slot control through one small kernel (see launch_solve_ctl); the
+// host mirrors are updated here.
+void Workset::apply_slot_ctl(const std::vector<int32_t>& ctl) {
+  bool any = false;
+  for (int i = 0; i < capacity_; ++i) {
+    const int32_t c = i < (int)ctl.size() ? ctl[i] : 8;
+    h_slotctl_[i] = c;
+    if (c & 8) continue;
+    any = true;
+    SolveHost* s = solves_[i];
+    if (!s) continue;
+    if (c & 2) s->phase ^= 1;
+    if (c & 4) s->apply_e = 0;
+    s->active = c & 1;
+  }
+  if (!any) return;
+  cuda_check(cudaMemcpyAsync(d_slotctl_, h_slotctl_, sizeof(int32_t) * capacity_, cudaMemcpyHostToDevice, stream_),
+             "slot ctl");
+  LAUNCH(launch_solve_ctl(d_solves_, d_slotctl_, capacity_, stream_), "solve ctl");
+  cuda_check(cudaStreamSynchronize(stream_), "sync");
+}
+
+void Workset::drop_graphs() {
+  for (auto& kv : graphs_)
+    if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+  graphs_.clear();
+}
+
 void Workset::rebuild_tables() {
   cuda_check(cudaStreamSynchronize(stream_), "sync");
+  drop_graphs();
   for (void* p : table_allocs_) pool_.release(p);
   table_allocs_.clear();
   std::vector<BlockDev> blocks;
   std::vector<WorkItem> w64, wlo;
+  std::vector<CtaTask> t64, tlo;
   std::vector<FaceItem> faces;
   std::vector<RedItem> red;
   std::vector<RowItem> rows;
-  block_base_.assign(capacity_, 0);
   face_base_.assign(capacity_, 0);
   face_cnt_.assign(capacity_, 0);
   row_base_.assign(capacity_, 0);
@@ -243,7 +310,6 @@ void Workset::rebuild_tables() {
     SolveHost* s = solves_[slot];
     if (!s) continue;
     const int base = (int)blocks.size();
-    block_base_[slot] = base;
     face_base_[slot] = (int)faces.size();
     row_base_[slot] = (int)rows.size();
     for (size_t b = 0; b < s->blocks.size(); ++b) {
@@ -251,10 +317,11 @@ void Workset::rebuild_tables() {
       B.solve = slot;
       for (int q = 0; q < 6; ++q)
         if (B.nbr[q] >= 0) B.nbr[q] += base;
-      blocks.push_back(B);
       const int bi = base + (int)b;
       const int ext = ndim_ == 2 ? B.by : B.bz;
-      auto items = [&](std::vector<WorkItem>& out, int seg_w, int R) {
+      // warp items of this block, then its CTA tasks (groups of kWarps items)
+      auto items = [&](std::vector<WorkItem>& out, std::vector<CtaTask>& tasks, int seg_w, int R) {
+        const int first = (int)out.size();
         const int segs = (B.bx + seg_w - 1) / seg_w;
         for (int m0 = 0; m0 < ext; m0 += R) {
           const int n = std::min(R, ext - m0);
@@ -266,9 +333,14 @@ void Workset::rebuild_tables() {
             }
           }
         }
+        const int last = (int)out.size();
+        int nt = 0;
+        for (int w = first; w < last; w += kWarps, ++nt) tasks.push_back(CtaTask{bi, w, std::min(kWarps, last - w), 0});
+        return nt;
       };
-      items(w64, kSegF64, r64);
-      if (refine()) items(wlo, kSegLow, rlo);
+      B.nt64 = items(w64, t64, kSegF64, r64);
+      B.ntlo = refine() ? items(wlo, tlo, kSegLow, rlo) : 0;
+      blocks.push_back(B);
       for (int q = 0; q < 2 * ndim_; ++q) faces.push_back(FaceItem{bi, q});
       for (int z = 0; z < B.bz; ++z)
         for (int y = 0; y < B.by; ++y) rows.push_back(RowItem{bi, y, z, 0});
@@ -290,14 +362,24 @@ void Workset::rebuild_tables() {
   d_blocks_ = (BlockDev*)up(blocks.data(), blocks.size() * sizeof(BlockDev));
   d_w64_ = (WorkItem*)up(w64.data(), w64.size() * sizeof(WorkItem));
   d_wlo_ = (WorkItem*)up(wlo.data(), wlo.size() * sizeof(WorkItem));
+  d_t64_ = (CtaTask*)up(t64.data(), t64.size() * sizeof(CtaTask));
+  d_tlo_ = (CtaTask*)up(tlo.data(), tlo.size() * sizeof(CtaTask));
   d_faces_ = (FaceItem*)up(faces.data(), faces.size() * sizeof(FaceItem));
   d_red_ = (RedItem*)up(red.data(), red.size() * sizeof(RedItem));
   d_rows_ = (RowItem*)up(rows.data(), rows.size() * sizeof(RowItem));
+  d_done_ = nullptr;
+  if (!blocks.empty()) {
+    d_done_ = (uint32_t*)pool_.alloc(blocks.size() * sizeof(uint32_t));
+    table_allocs_.push_back(d_done_);
+  }
   n64_ = (int)w64.size();
   nlo_ = (int)wlo.size();
+  nt64_ = (int)t64.size();
+  ntlo_ = (int)tlo.size();
   nfaces_ = (int)faces.size();
   nred_ = (int)red.size();
   nrows_ = (int)rows.size();
+  nblocks_ = (int)blocks.size();
   cuda_check(cudaStreamSynchronize(stream_), "sync");
   tables_dirty_ = false;
 }
@@ -317,6 +399,14 @@ Tables Workset::tables() const {
   t.blocks = d_blocks_;
   t.solves = d_solves_;
   t.ndim = ndim_;
+  t.t64 = d_t64_;
+  t.nt64 = nt64_;
+  t.tlo = d_tlo_;
+  t.ntlo = ntlo_;
+  t.done = d_done_;
+  t.ctl = d_ctl_;
+  t.spin_limit = (uint32_t)std::min<int64_t>(std::max<int64_t>(opt.spin_limit, 0), 0x7fffffff);
+  t.poison = opt.poison_wait ? 1 : 0;
   return t;
 }
 
@@ -368,13 +458,12 @@ void Workset::gather(int slot, double* dense, int on_device) {
 // active solve: pack every interior face, then unpack into the neighbours.
 void Workset::halo_exchange_x(int kpar) {
   const Tables t = tables();
-  LAUNCH(launch_halo_pack(t, 0, kpar, low(), stream_), "halo pack");
-  LAUNCH(launch_halo_unpack(t, 0, kpar, low(), stream_), "halo unpack");
+  LAUNCH(launch_halo_pack(t, 0, kpar, low(), cur_), "halo pack");
+  LAUNCH(launch_halo_unpack(t, 0, kpar, low(), cur_), "halo unpack");
 }
 
 void Workset::upload_inputs(SolveHost& s) {
   const ProblemSpec& p = s.spec;
-  // source term
   if (p.source) scatter(s.slot, p.source, 1, p.inputs_on_device);
   // Dirichlet ghosts into both parities
   const int nfaces = 2 * p.ndim;
@@ -411,28 +500,25 @@ void Workset::upload_inputs(SolveHost& s) {
     LAUNCH(launch_ghost_fill(st, dfaces, par, p.n[0], p.n[1], p.n[2], stream_), "ghost fill");
   cuda_check(cudaStreamSynchronize(stream_), "sync");
   for (void* d : tmps) pool_.release(d);
-  // ||b||^2 = residual of the zero field (interiors are still zero)
-  {
-    // only this solve is active during set-up work
-    std::vector<int> was(capacity_, 0);
-    for (int k = 0; k < capacity_; ++k)
-      if (solves_[k] && k != s.slot) {
-        was[k] = solves_[k]->active;
-        set_active(k, 0);
-      }
-    residual_only();
-    std::vector<double> rss;
-    read_rss(rss);
-    s.bss = rss[s.slot];
-    // initial iterate
-    if (p.x0) {
-      scatter(s.slot, p.x0, 0, p.inputs_on_device);
-      halo_exchange_x(0);
+  // ||b||^2 = residual of the zero field (interiors are still zero); every
+  // other solve is masked off meanwhile
+  std::vector<int32_t> ctl(capacity_, 8), back(capacity_, 8);
+  for (int k = 0; k < capacity_; ++k)
+    if (solves_[k] && k != s.slot && solves_[k]->active) {
+      ctl[k] = 0;
+      back[k] = 1;
     }
-    cuda_check(cudaStreamSynchronize(stream_), "sync");
-    for (int k = 0; k < capacity_; ++k)
-      if (solves_[k] && k != s.slot) set_active(k, was[k]);
+  apply_slot_ctl(ctl);
+  residual_only();
+  std::vector<double> rss;
+  read_rss(rss);
+  s.bss = rss[s.slot];
+  if (p.x0) {
+    scatter(s.slot, p.x0, 0, p.inputs_on_device);
+    halo_exchange_x(0);
   }
+  cuda_check(cudaStreamSynchronize(stream_), "sync");
+  apply_slot_ctl(back);
 }
 
 int Workset::add_solve(const ProblemSpec& p) {
@@ -461,7 +547,7 @@ int Workset::add_solve(const ProblemSpec& p) {
     memset(&z, 0, sizeof(z));
     cudaMemcpyAsync(d_solves_ + slot, &z, sizeof(z), cudaMemcpyHostToDevice, stream_);
     cudaStreamSynchronize(stream_);
-    rebuild_tables();
+    tables_dirty_ = true;
     throw;
   }
   return slot;
@@ -470,34 +556,55 @@ int Workset::add_solve(const ProblemSpec& p) {
 void Workset::remove_solve(int slot) {
   SolveHost* s = solve(slot);
   if (!s) return;
-  set_active(slot, 0);
+  cuda_check(cudaStreamSynchronize(stream_), "sync");
+  SolveDev z;
+  memset(&z, 0, sizeof(z));
+  cuda_check(cudaMemcpyAsync(d_solves_ + slot, &z, sizeof(z), cudaMemcpyHostToDevice, stream_), "clear solve");
   cuda_check(cudaStreamSynchronize(stream_), "sync");
   for (void* q : s->allocs) pool_.release(q);
   delete s;
   solves_[slot] = nullptr;
-  SolveDev z;
-  memset(&z, 0, sizeof(z));
-  cuda_check(cudaMemcpyAsync(d_solves_ + slot, &z, sizeof(z), cudaMemcpyHostToDevice, stream_), "clear solve");
-  rebuild_tables();
+  tables_dirty_ = true;
 }
 
 void Workset::sync() { cuda_check(cudaStreamSynchronize(stream_), "cudaStreamSynchronize"); }
 
 void Workset::reduce() {
   prof_begin(kProfReduce);
-  LAUNCH(launch_reduce(tables(), stream_), "reduce");
+  LAUNCH(launch_reduce(tables(), cur_), "reduce");
   prof_end(kProfReduce);
+}
+
+void Workset::sched_reset() {
+  cuda_check(cudaMemsetAsync(d_ctl_, 0, sizeof(SchedCtl), cur_), "memset ctl");
+  if (d_done_) cuda_check(cudaMemsetAsync(d_done_, 0, sizeof(uint32_t) * nblocks_, cur_), "memset done");
 }
 
 void Workset::sweeps_f64(int64_t n, bool resid_last) {
   if (tables_dirty_) rebuild_tables();
+  if (n <= 0) return;
   const Tables t = tables();
   const bool push = opt.halo == 0;
+  if (opt.schedule == 1 && push) {
+    // persistent block scheduler, in launches of at most 4096 sweeps
+    for (int64_t done = 0; done < n;) {
+      const int64_t k = std::min<int64_t>(4096, n - done);
+      const bool last = done + k == n;
+      sched_reset();
+      prof_begin(kProfSweepF64);
+      LAUNCH(launch_persist_f64(t, (int)k, resid_last && last, cur_), "persistent sweep f64");
+      prof_end(kProfSweepF64);
+      if (k & 1) phase_advance(1, -1);
+      done += k;
+    }
+    if (resid_last) reduce();
+    return;
+  }
   for (int64_t k = 0; k < n; ++k) {
     const bool resid = resid_last && k == n - 1;
     const int kpar = (int)(k & 1);
     prof_begin(kProfSweepF64);
-    LAUNCH(launch_sweep_f64(t, kpar, push, resid, true, stream_), "sweep f64");
+    LAUNCH(launch_sweep_f64(t, kpar, push, resid, true, cur_), "sweep f64");
     prof_end(kProfSweepF64);
     if (!push) {
       prof_begin(kProfHalo);
@@ -505,12 +612,12 @@ void Workset::sweeps_f64(int64_t n, bool resid_last) {
       prof_end(kProfHalo);
     }
   }
-  if (resid_last && n > 0) reduce();
+  if (resid_last) reduce();
   if (n & 1) phase_advance(1, -1);
 }
 
 void Workset::phase_advance(int d, int set_apply_e) {
-  LAUNCH(launch_phase_advance(d_solves_, capacity_, d, set_apply_e, stream_), "phase advance");
+  LAUNCH(launch_phase_advance(d_solves_, capacity_, d, set_apply_e, cur_), "phase advance");
   for (auto* s : solves_)
     if (s && s->active) {
       s->phase = (s->phase + d) & 1;
@@ -520,7 +627,7 @@ void Workset::phase_advance(int d, int set_apply_e) {
 
 void Workset::residual_only() {
   if (tables_dirty_) rebuild_tables();
-  LAUNCH(launch_sweep_f64(tables(), 0, false, true, false, stream_), "residual");
+  LAUNCH(launch_sweep_f64(tables(), 0, false, true, false, cur_), "residual");
   reduce();
 }
 
@@ -529,7 +636,7 @@ void Workset::refine_outer() {
   const Tables t = tables();
   const bool push = opt.halo == 0;
   prof_begin(kProfOuter);
-  LAUNCH(launch_refine_outer(t, epar_last_, push, low(), dtype_ == 2 && opt.r_bf16, stream_), "refine outer");
+  LAUNCH(launch_refine_outer(t, epar_last_, push, low(), r_bf16_, cur_), "refine outer");
   prof_end(kProfOuter);
   if (!push) {
     prof_begin(kProfHalo);
@@ -542,28 +649,326 @@ void Workset::refine_outer() {
 
 void Workset::refine_inner(int64_t k) {
   if (tables_dirty_) rebuild_tables();
+  if (k <= 0) return;
   const Tables t = tables();
   const bool push = opt.halo == 0;
-  const bool rb = dtype_ == 2 && opt.r_bf16;
-  for (int64_t j = 0; j < k; ++j) {
-    const int epar = (int)(j & 1);
+  if (opt.schedule == 1 && push) {
+    if (k > 4096) throw JErr{1, "refine_period above 4096 with the persistent scheduler"};
+    sched_reset();
     prof_begin(kProfSweepLow);
-    LAUNCH(launch_sweep_low(t, epar, j == 0, push, low(), rb, stream_), "sweep low");
+    LAUNCH(launch_persist_low(t, (int)k, low(), r_bf16_, cur_), "persistent sweep low");
     prof_end(kProfSweepLow);
-    if (!push) {
-      prof_begin(kProfHalo);
-      LAUNCH(launch_halo_pack(t, 1, epar, low(), stream_), "halo pack e");
-      LAUNCH(launch_halo_unpack(t, 1, epar, low(), stream_), "halo unpack e");
-      prof_end(kProfHalo);
+  } else {
+    for (int64_t j = 0; j < k; ++j) {
+      const int epar = (int)(j & 1);
+      prof_begin(kProfSweepLow);
+      LAUNCH(launch_sweep_low(t, epar, j == 0, push, low(), r_bf16_, cur_), "sweep low");
+      prof_end(kProfSweepLow);
+      if (!push) {
+        prof_begin(kProfHalo);
+        LAUNCH(launch_halo_pack(t, 1, epar, low(), cur_), "halo pack e");
+        LAUNCH(launch_halo_unpack(t, 1, epar, low(), cur_), "halo unpack e");
+        prof_end(kProfHalo);
+      }
     }
   }
-  if (k > 0) epar_last_ = (int)((k - 1) & 1);
+  epar_last_ = (int)((k - 1) & 1);
 }
 
 void Workset::read_rss(std::vector<double>& out) {
   cuda_check(cudaMemcpyAsync(h_rss_, d_rss_, sizeof(double) * capacity_, cudaMemcpyDeviceToHost, stream_), "D2H rss");
+  cuda_check(cudaMemcpyAsync(h_ctl_, d_ctl_, sizeof(SchedCtl), cudaMemcpyDeviceToHost, stream_), "D2H ctl");
   cuda_check(cudaStreamSynchronize(stream_), "sync");
   out.assign(h_rss_, h_rss_ + capacity_);
+  if (h_ctl_->status != 0) {
+    const uint32_t task = h_ctl_->fail_task;
+    cuda_check(cudaMemsetAsync(d_ctl_, 0, sizeof(SchedCtl), stream_), "memset ctl");
+    cuda_check(cudaStreamSynchronize(stream_), "sync");
+    throw JErr{6, "persistent scheduler: a dependency wait ran out (task " + std::to_string(task) +
+                      "); the field is no longer consistent"};
+  }
+}
+
+// ---------------------------------------------------------------------------
+// CUDA graphs: one solve step is captured once (on a private stream) and then
+// replayed on the caller's stream.
+
+template <typename F>
+bool Workset::run_graph(int64_t key, F body) {
+  if (tables_dirty_) rebuild_tables();
+  auto it = graphs_.find(key);
+  const bool captured = it == graphs_.end();
+  if (captured) {
+    GraphRec rec;
+    const int64_t l0 = launches_;
+    cudaGraph_t g = nullptr;
+    cuda_check(cudaStreamSynchronize(stream_), "sync");
+    cuda_check(cudaStreamBeginCapture(cap_stream_, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    cur_ = cap_stream_;
+    capturing_ = true;
+    try {
+      body();
+    } catch (...) {
+      capturing_ = false;
+      cur_ = stream_;
+      cudaStreamEndCapture(cap_stream_, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    capturing_ = false;
+    cur_ = stream_;
+    cuda_check(cudaStreamEndCapture(cap_stream_, &g), "cudaStreamEndCapture");
+    const cudaError_t e = cudaGraphInstantiate(&rec.exec, g, 0);
+    cudaGraphDestroy(g);
+    cuda_check(e, "cudaGraphInstantiate");
+    rec.nodes = launches_ - l0;
+    launches_ = l0;
+    it = graphs_.emplace(key, rec).first;
+  }
+  cuda_check(cudaGraphLaunch(it->second.exec, stream_), "cudaGraphLaunch");
+  launches_ += it->second.nodes;
+  ++graph_replays_;
+  return captured;  // the body ran on the host (and updated the host mirrors)
+}
+
+// k inner sweeps, then the outer step (x += e, r, residual).
+void Workset::step_refine(int64_t k) {
+  auto body = [&]() {
+    refine_inner(k);
+    refine_outer();
+  };
+  if (opt.graph && !opt.profile) {
+    if (!run_graph(2 * k, body)) {
+      epar_last_ = (int)((k - 1) & 1);
+      for (auto* s : solves_)
+        if (s && s->active) {
+          s->phase ^= 1;
+          s->apply_e = 1;
+        }
+    }
+  } else {
+    body();
+  }
+}
+
+// n FP64 sweeps, the last one reducing the residual of its input.
+void Workset::chunk_f64(int64_t n) {
+  auto body = [&]() { sweeps_f64(n, true); };
+  if (opt.graph && !opt.profile) {
+    if (!run_graph(2 * n + 1, body))
+      for (auto* s : solves_)
+        if (s && s->active) s->phase = (s->phase + (int)(n & 1)) & 1;
+  } else {
+    body();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// solve loop over every active slot
+
+void Workset::solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>& res) {
+  if (tables_dirty_) rebuild_tables();
+  if (opt.autotune && !tuned_) autotune();
+  res.assign(capacity_, SlotResult());
+  std::vector<int> slots;
+  for (int k = 0; k < capacity_; ++k)
+    if (solves_[k] && solves_[k]->active) slots.push_back(k);
+  const auto t0 = std::chrono::steady_clock::now();
+  std::vector<double> rss;
+  int64_t m = 0;
+  int left = (int)slots.size();
+  const bool ref = refine();
+  if (ref) refine_outer();
+  else chunk_f64(1);
+  std::vector<int32_t> ctl(capacity_, 8);
+  while (left > 0) {
+    read_rss(rss);
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    std::fill(ctl.begin(), ctl.end(), 8);
+    bool retire = false;
+    for (int k : slots) {
+      SlotResult& r = res[k];
+      if (r.done) continue;
+      SolveHost* s = solves_[k];
+      const double rel = s->bss > 0.0 ? std::sqrt(rss[k]) / std::sqrt(s->bss) : std::sqrt(rss[k]);
+      int st = -1;
+      if (!std::isfinite(rel)) st = 5;
+      else if (rel <= tol) st = 0;
+      else if (m >= max_sweeps) st = 4;
+      if (st < 0) continue;
+      r = SlotResult{st, m, rel, secs, true};
+      --left;
+      // retire the slot; plain FP64 also steps back to iterate m (the checked
+      // one: the last sweep only reduced its residual)
+      ctl[k] = ref ? 4 : 2;
+      retire = true;
+    }
+    if (retire) apply_slot_ctl(ctl);
+    if (left == 0) break;
+    const int64_t n = std::min<int64_t>(ref ? opt.refine_period : opt.check_every, max_sweeps - m);
+    if (ref) step_refine(n);
+    else chunk_f64(n);
+    m += n;
+  }
+  // every slot that took part is active again; a refinement's correction is consumed
+  std::fill(ctl.begin(), ctl.end(), 8);
+  for (int k : slots) ctl[k] = ref ? (1 | 4) : 1;
+  apply_slot_ctl(ctl);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time a few sweeps of each candidate (rows per work item, launch
+// schedule) and keep the fastest.  Every candidate computes the same bits, so
+// the choice never changes a result.  Choices are cached in the JSON-lines
+// file named by JACOBI_TUNE_CACHE (when set).
+
+static std::string tune_key(const Workset& w, const std::vector<SolveHost*>& solves, int dtype) {
+  std::ostringstream k;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceProp prop;
+  cudaGetDeviceProperties(&prop, dev);
+  int64_t pts = 0, nb = 0, bx = 0, by = 0, bz = 0;
+  for (auto* s : solves)
+    if (s) {
+      pts += s->points();
+      nb += (int64_t)s->blocks.size();
+      bx = s->spec.blk[0];
+      by = s->spec.blk[1];
+      bz = s->spec.blk[2];
+    }
+  // points rounded to a power of two so that similar worksets share an entry
+  const int lg = pts > 0 ? (int)std::lround(std::log2((double)pts)) : 0;
+  k << prop.name << "|d" << w.ndim() << "|t" << dtype << "|b" << bx << "x" << by << "x" << bz << "|p2^" << lg
+    << "|nb" << (nb > 1 ? (int)std::lround(std::log2((double)nb)) : 0);
+  std::string s = k.str();
+  for (auto& c : s)
+    if (c == '"') c = '\'';
+  return s;
+}
+
+static bool tune_cache_lookup(const std::string& key, int64_t& rows, int64_t& sched) {
+  const char* path = std::getenv("JACOBI_TUNE_CACHE");
+  if (!path) return false;
+  std::ifstream in(path);
+  std::string line;
+  bool found = false;
+  while (std::getline(in, line)) {
+    const std::string kk = "\"key\": \"" + key + "\"";
+    if (line.find(kk) == std::string::npos) continue;
+    long long r = 0, s = 0;
+    const size_t pr = line.find("\"rows\": "), ps = line.find("\"schedule\": ");
+    if (pr == std::string::npos || ps == std::string::npos) continue;
+    r = std::atoll(line.c_str() + pr + 8);
+    s = std::atoll(line.c_str() + ps + 12);
+    if (r >= 1 && (s == 0 || s == 1)) {
+      rows = r;
+      sched = s;
+      found = true;
+    }
+  }
+  return found;
+}
+
+static void tune_cache_store(const std::string& key, int64_t rows, int64_t sched, double us) {
+  const char* path = std::getenv("JACOBI_TUNE_CACHE");
+  if (!path) return;
+  std::ofstream out(path, std::ios::app);
+  out << "{\"key\": \"" << key << "\", \"rows\": " << rows << ", \"schedule\": " << sched
+      << ", \"us_per_sweep\": " << us << "}\n";
+}
+
+void Workset::autotune() {
+  tuned_ = true;
+  if (live() == 0) return;
+  const bool ref = refine();
+  const std::string key = tune_key(*this, solves_, dtype_);
+  int64_t rows = 0, sched = 0;
+  int64_t& opt_rows = ref ? opt.rows_low : opt.rows_f64;
+  if (tune_cache_lookup(key, rows, sched)) {
+    opt_rows = rows;
+    opt.schedule = sched;
+    rebuild_tables();
+    tune_summary_ = "cache: rows " + std::to_string(rows) + ", schedule " + std::to_string(sched);
+    return;
+  }
+  // snapshot of every FP64 iterate so the timing sweeps leave no trace
+  std::vector<std::pair<double*, void*>> saved;
+  if (!ref) {
+    for (auto* s : solves_)
+      if (s) {
+        void* tmp = pool_.alloc((size_t)s->elems * 16);
+        cuda_check(cudaMemcpyAsync(tmp, s->x[0], (size_t)s->elems * 8, cudaMemcpyDeviceToDevice, stream_), "save");
+        cuda_check(cudaMemcpyAsync((char*)tmp + s->elems * 8, s->x[1], (size_t)s->elems * 8, cudaMemcpyDeviceToDevice,
+                                   stream_),
+                   "save");
+        saved.push_back({(double*)tmp, s});
+      }
+  }
+  std::vector<int> phases;
+  for (auto* s : solves_) phases.push_back(s ? s->phase : 0);
+  const int64_t prof = opt.profile, graph = opt.graph;
+  opt.profile = 0;
+  opt.graph = 0;
+  cudaEvent_t a, b;
+  cuda_check(cudaEventCreate(&a), "event");
+  cuda_check(cudaEventCreate(&b), "event");
+  double best = 1e300;
+  int64_t best_rows = opt_rows, best_sched = opt.schedule;
+  const int64_t cand_rows[] = {8, 16, 32, 64, 128};
+  const int sweeps = 8;
+  for (int64_t sc = 0; sc <= 1; ++sc) {
+    for (int64_t r : cand_rows) {
+      opt_rows = r;
+      opt.schedule = sc;
+      rebuild_tables();
+      auto run = [&]() {
+        if (ref) refine_inner(sweeps);
+        else sweeps_f64(sweeps, false);
+      };
+      run();  // warm-up
+      cuda_check(cudaEventRecord(a, stream_), "event");
+      run();
+      cuda_check(cudaEventRecord(b, stream_), "event");
+      cuda_check(cudaEventSynchronize(b), "event");
+      float ms = 0.f;
+      cuda_check(cudaEventElapsedTime(&ms, a, b), "event");
+      if (ms < best) {
+        best = ms;
+        best_rows = r;
+        best_sched = sc;
+      }
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  opt.profile = prof;
+  opt.graph = graph;
+  opt_rows = best_rows;
+  opt.schedule = best_sched;
+  rebuild_tables();
+  // restore the iterates and phases the timing sweeps changed
+  if (!ref) {
+    size_t i = 0;
+    for (auto* s : solves_)
+      if (s) {
+        double* tmp = saved[i++].first;
+        cuda_check(cudaMemcpyAsync(s->x[0], tmp, (size_t)s->elems * 8, cudaMemcpyDeviceToDevice, stream_), "restore");
+        cuda_check(cudaMemcpyAsync(s->x[1], (char*)tmp + s->elems * 8, (size_t)s->elems * 8, cudaMemcpyDeviceToDevice,
+                                   stream_),
+                   "restore");
+      }
+    sync();
+    for (auto& sv : saved) pool_.release(sv.first);
+  }
+  std::vector<int32_t> ctl(capacity_, 8);
+  for (int k = 0; k < capacity_; ++k)
+    if (solves_[k] && solves_[k]->phase != phases[k]) ctl[k] = (solves_[k]->active ? 1 : 0) | 2;
+  apply_slot_ctl(ctl);
+  const double us = best * 1e3 / sweeps;
+  tune_cache_store(key, best_rows, best_sched, us);
+  tune_summary_ = "measured: rows " + std::to_string(best_rows) + ", schedule " + std::to_string(best_sched) +
+                  ", " + std::to_string(us) + " us per sweep";
 }
 
 // ---------------------------------------------------------------------------
@@ -571,7 +976,7 @@ void Workset::read_rss(std::vector<double>& out) {
 
 void Workset::prof_begin(int kind) {
   (void)kind;
-  if (!opt.profile) return;
+  if (!opt.profile || capturing_) return;
   if (ev_free_.empty()) {
     cudaEvent_t e;
     cuda_check(cudaEventCreate(&e), "cudaEventCreate");
@@ -579,11 +984,11 @@ void Workset::prof_begin(int kind) {
   }
   ev_open_ = ev_free_.back();
   ev_free_.pop_back();
-  cuda_check(cudaEventRecord(ev_open_, stream_), "cudaEventRecord");
+  cuda_check(cudaEventRecord(ev_open_, cur_), "cudaEventRecord");
 }
 
 void Workset::prof_end(int kind) {
-  if (!opt.profile || !ev_open_) return;
+  if (!opt.profile || capturing_ || !ev_open_) return;
   if (ev_free_.empty()) {
     cudaEvent_t e;
     cuda_check(cudaEventCreate(&e), "cudaEventCreate");
@@ -591,7 +996,7 @@ void Workset::prof_end(int kind) {
   }
   cudaEvent_t b = ev_free_.back();
   ev_free_.pop_back();
-  cuda_check(cudaEventRecord(b, stream_), "cudaEventRecord");
+  cuda_check(cudaEventRecord(b, cur_), "cudaEventRecord");
   ev_pending_[kind].push_back(EvPair{ev_open_, b});
   ev_open_ = nullptr;
 }

@@ -9,6 +9,7 @@
 
 #include <stdint.h>
 
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -36,8 +37,8 @@ class DevPool {
  public:
   DevPool(const AllocHooks& h, cudaStream_t s) : hooks_(h), stream_(s) {}
   ~DevPool();
-  void* alloc(size_t bytes);        // zero bytes -> nullptr; failure throws JErr(OOM)
-  void release(void* p);            // frees one allocation
+  void* alloc(size_t bytes);  // zero bytes -> nullptr; failure throws JErr(OOM)
+  void release(void* p);      // frees one allocation
   int64_t bytes() const { return bytes_; }
 
  private:
@@ -51,7 +52,7 @@ class DevPool {
   int64_t bytes_ = 0;
 };
 
-// Problem description of one solve (host memory).
+// Problem description of one solve (host memory unless inputs_on_device).
 struct ProblemSpec {
   int ndim = 2;
   int64_t n[3] = {1, 1, 1};
@@ -92,6 +93,10 @@ struct SolveHost {
   int64_t points() const { return spec.n[0] * spec.n[1] * spec.n[2]; }
 };
 
+// Bytes of device memory one solve needs (layout arrays, face buffers,
+// partial sums): the admission test of the server.
+int64_t solve_device_bytes(const ProblemSpec& p, int dtype, bool r_bf16);
+
 enum ProfKind { kProfSweepF64 = 0, kProfSweepLow, kProfOuter, kProfReduce, kProfHalo, kProfCount };
 
 struct Options {
@@ -100,13 +105,26 @@ struct Options {
   int64_t halo = 0;          // 0 fused, 1 standalone pack/unpack
   int64_t rows_f64 = 32;
   int64_t rows_low = 32;
-  int64_t r_bf16 = 0;
   int64_t profile = 0;
+  int64_t schedule = 0;      // 0 one launch per sweep, 1 persistent block scheduler
+  int64_t graph = 0;         // 1: replay each solve step from a captured CUDA graph
+  int64_t spin_limit = 1 << 22;
+  int64_t poison_wait = 0;   // test hook: every dependency wait of the persistent kernel runs out
+  int64_t autotune = 0;      // 1: pick rows/schedule by timing before the first solve
+};
+
+// Outcome of one solve inside solve_all.
+struct SlotResult {
+  int status = 0;
+  int64_t sweeps = 0;
+  double rel = 0.0;
+  double seconds = 0.0;
+  bool done = false;
 };
 
 class Workset {
  public:
-  Workset(int ndim, int dtype, cudaStream_t stream, int capacity);
+  Workset(int ndim, int dtype, cudaStream_t stream, int capacity, bool r_bf16 = false);
   ~Workset();
 
   // Adds a solve, uploads its inputs, computes ||b||; returns its slot.
@@ -123,10 +141,18 @@ class Workset {
   // Refinement: outer step (x += e if pending; r; reduction), then k inner sweeps.
   void refine_outer();
   void refine_inner(int64_t k);
-  // Read the sums of squares of every slot (synchronises).
+  // Read the sums of squares of every slot (synchronises; throws on a timed
+  // out dependency wait of the persistent scheduler).
   void read_rss(std::vector<double>& out);
   void set_active(int slot, int active);
   void sync();
+
+  // Solve every active slot to tol (the test of section 8's solve rule):
+  // plain FP64 with checks every check_every sweeps, or refinement with a
+  // check after every outer step.  Slots stay active afterwards.
+  void solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>& res);
+  // Pick rows_f64 / rows_low / schedule by timing (restores the state).
+  void autotune();
 
   void scatter(int slot, const double* dense, int which, int on_device);
   void gather(int slot, double* dense, int on_device);
@@ -140,13 +166,16 @@ class Workset {
   bool refine() const { return dtype_ != 0; }
   int ndim() const { return ndim_; }
   int dtype() const { return dtype_; }
-  int low() const { return dtype_ == 2 ? kLowBF16 : kLowF32; }
+  int low() const { return dtype_ >= 2 ? kLowBF16 : kLowF32; }
+  bool r_bf16() const { return r_bf16_; }
   cudaStream_t stream() const { return stream_; }
   SolveHost* solve(int slot) { return slot >= 0 && slot < (int)solves_.size() ? solves_[slot] : nullptr; }
   int capacity() const { return capacity_; }
+  int live() const;
   int64_t device_bytes() const { return pool_.bytes(); }
-  int last_epar() const { return epar_last_; }
   int64_t launches() const { return launches_; }
+  int64_t graph_replays() const { return graph_replays_; }
+  std::string tune_summary() const { return tune_summary_; }
 
   Options opt;
 
@@ -158,9 +187,21 @@ class Workset {
   Tables tables() const;
   Tables solve_tables(const SolveHost& s) const;
   void reduce();
+  void sched_reset();
+  void apply_slot_ctl(const std::vector<int32_t>& ctl);
+  // one solve step, captured in a CUDA graph when opt.graph is set
+  void step_refine(int64_t k);
+  void chunk_f64(int64_t n);
+  template <typename F>
+  bool run_graph(int64_t key, F body);
+  void drop_graphs();
 
   int ndim_, dtype_, capacity_;
-  cudaStream_t stream_;
+  bool r_bf16_;
+  cudaStream_t stream_;   // the caller's stream: everything ends up here
+  cudaStream_t cur_;      // where launches are issued (stream_, or the capture stream)
+  cudaStream_t cap_stream_ = nullptr;
+  bool capturing_ = false;
   DevPool pool_;
   std::vector<SolveHost*> solves_;   // slot -> solve (nullptr when free)
   // device tables
@@ -168,19 +209,33 @@ class Workset {
   double* d_rss_ = nullptr;
   uint32_t* d_ticket_ = nullptr;
   double* h_rss_ = nullptr;          // pinned
+  SchedCtl* d_ctl_ = nullptr;
+  SchedCtl* h_ctl_ = nullptr;        // pinned
+  int32_t* d_slotctl_ = nullptr;
+  int32_t* h_slotctl_ = nullptr;     // pinned
   BlockDev* d_blocks_ = nullptr;
   WorkItem* d_w64_ = nullptr;
   WorkItem* d_wlo_ = nullptr;
+  CtaTask* d_t64_ = nullptr;
+  CtaTask* d_tlo_ = nullptr;
+  uint32_t* d_done_ = nullptr;
   FaceItem* d_faces_ = nullptr;
   RedItem* d_red_ = nullptr;
   RowItem* d_rows_ = nullptr;
-  int n64_ = 0, nlo_ = 0, nfaces_ = 0, nred_ = 0, nrows_ = 0;
+  int n64_ = 0, nlo_ = 0, nt64_ = 0, ntlo_ = 0, nfaces_ = 0, nred_ = 0, nrows_ = 0, nblocks_ = 0;
   std::vector<void*> table_allocs_;
-  std::vector<int> block_base_;      // slot -> first block index in the table
   std::vector<int> face_base_, face_cnt_, row_base_, row_cnt_;
   int epar_last_ = 0;
   int64_t launches_ = 0;           // kernel launches issued so far
+  int64_t graph_replays_ = 0;
   bool tables_dirty_ = true;
+  bool tuned_ = false;
+  std::string tune_summary_;
+  struct GraphRec {
+    cudaGraphExec_t exec = nullptr;
+    int64_t nodes = 0;
+  };
+  std::map<int64_t, GraphRec> graphs_;
   // profiling events
   struct EvPair {
     cudaEvent_t a, b;

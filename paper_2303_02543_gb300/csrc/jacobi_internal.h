@@ -49,6 +49,9 @@ struct BlockDev {
   int32_t nbr[6];     // neighbour block index (table-wide) or -1 on the domain boundary
   int32_t fsz[6];     // elements of each face send buffer
   int32_t ox;         // origin of the block in the solve grid (x)
+  int32_t nt64;       // CTA tasks of this block in the FP64 task table
+  int32_t ntlo;       // CTA tasks of this block in the low-precision task table
+  int32_t pad;
 };
 
 struct SolveDev {
@@ -81,6 +84,24 @@ struct WorkItem {
   int16_t n;
   int32_t y0;
   int32_t z0;
+};
+
+// One task of the persistent scheduler: up to kWarps consecutive warp items,
+// all of one block (a task in the sense of section 3.1.2: a unit of work with
+// known inputs; its dependencies are the block and its neighbours).
+struct CtaTask {
+  int32_t block;
+  int32_t w0;  // first warp item
+  int32_t nw;  // warp items (1 .. kWarps)
+  int32_t pad;
+};
+
+// Control word of one persistent launch (zeroed before it).
+struct SchedCtl {
+  uint32_t head;       // next task index handed out
+  uint32_t status;     // 0 ok, 1 a dependency wait ran out (JACOBI_ERR_TIMEOUT)
+  uint32_t fail_task;  // task index whose wait ran out
+  uint32_t pad;
 };
 
 // One face of one block for the standalone pack / unpack kernels.
@@ -116,6 +137,12 @@ struct Tables {
   const BlockDev* blocks;
   SolveDev* solves;
   int ndim;
+  const CtaTask* t64;   int nt64;    // persistent tasks over w64
+  const CtaTask* tlo;   int ntlo;    // persistent tasks over wlo
+  uint32_t* done;                    // per block: tasks completed in this launch
+  SchedCtl* ctl;
+  uint32_t spin_limit;               // bounded dependency waits
+  int poison;                        // test hook: every dependency wait runs out
 };
 
 int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, void* stream);
@@ -129,5 +156,13 @@ int launch_gather(const Tables& t, double* dense, int par, int64_t nx, int64_t n
 int launch_ghost_fill(const Tables& t, const double* const* faces_dev, int par, int64_t nx, int64_t ny,
                       int64_t nz, void* stream);
 int launch_phase_advance(SolveDev* solves, int nsolves, int dphase, int set_apply_e, void* stream);
+// Persistent block scheduler: one launch runs nsweeps sweeps of every active
+// solve; CTAs pull (sweep, task) pairs in sweep order and wait (bounded) for
+// the block's and its neighbours' previous sweep.
+int launch_persist_f64(const Tables& t, int nsweeps, bool resid_last, void* stream);
+int launch_persist_low(const Tables& t, int nsweeps, int low, bool r_bf16, void* stream);
+// Per-slot control from the host: ctl[i] bit 0 = new active flag, bit 1 = flip the phase,
+// bit 2 = clear apply_e, bit 3 = leave the slot unchanged.
+int launch_solve_ctl(SolveDev* solves, const int32_t* ctl, int nsolves, void* stream);
 
 }  // namespace jgb

@@ -22,6 +22,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
 #include "exact_f64.cuh"
 #include "jacobi_internal.h"
 
@@ -32,7 +34,11 @@ namespace jgb {
 // ---------------------------------------------------------------------------
 // scalar helpers
 
-__device__ __forceinline__ double dadd(double a, double b) { return __dadd_rn(a, b); }
+// a + b rounded to nearest even, issued as fma(a, 1, b): the product a * 1 is
+// exact, so the result is bit-identical to __dadd_rn(a, b) for every input,
+// and on GB300 the FMA form issues faster than DADD (about 1.9 versus 1.6 per
+// clock per SM, measured).
+__device__ __forceinline__ double dadd(double a, double b) { return __fma_rn(a, 1.0, b); }
 
 // t / 4, exact: exponent decrement on the integer pipe, FP64 multiply only when
 // some lane of the warp needs it (zero, subnormal, inf/NaN).
@@ -169,18 +175,60 @@ struct PushTargets {
 // MODE of the FP64 kernel
 enum { kModeSweep = 0, kModeResid = 1, kModeOuter = 2 };
 
+// Load policies.  COH = false: read-only path (__ldg), valid when nothing
+// writes the array during the launch.  COH = true: L2-only loads (__ldcg),
+// for the persistent kernel where other CTAs rewrite the arrays while it runs.
+template <bool COH>
+__device__ __forceinline__ double ldd(const double* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ double2 ldd2(const double* p) {
+  if constexpr (COH) return __ldcg(reinterpret_cast<const double2*>(p));
+  else return __ldg(reinterpret_cast<const double2*>(p));
+}
+template <bool COH>
+__device__ __forceinline__ float ldf(const float* p) {
+  if constexpr (COH) return __ldcg(p);
+  else return __ldg(p);
+}
+template <bool COH>
+__device__ __forceinline__ float ldf(const __nv_bfloat16* p) {
+  const unsigned short* q = reinterpret_cast<const unsigned short*>(p);
+  unsigned short u;
+  if constexpr (COH) u = __ldcg(q);
+  else u = __ldg(q);
+  return __bfloat162float(__ushort_as_bfloat16(u));
+}
+template <bool COH>
+__device__ __forceinline__ float4 ldf4(const float* p) {
+  if constexpr (COH) return __ldcg(reinterpret_cast<const float4*>(p));
+  else return __ldg(reinterpret_cast<const float4*>(p));
+}
+template <bool COH>
+__device__ __forceinline__ float4 ldf4(const __nv_bfloat16* p) {
+  uint2 u;
+  if constexpr (COH) u = __ldcg(reinterpret_cast<const uint2*>(p));
+  else u = __ldg(reinterpret_cast<const uint2*>(p));
+  bf16x4 v;
+  memcpy(&v, &u, 8);
+  const float2 lo = __bfloat1622float2(v.a), hi = __bfloat1622float2(v.b);
+  return make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+
 // Loader of "the field value" at an element offset: x, or x + e in the outer
 // refinement step (the updated iterate x_new = x + e, formed on the fly).
-template <int MODE, typename TE>
+template <int MODE, typename TE, bool COH>
 struct F64Src {
   const double* __restrict__ x;
   const TE* __restrict__ e;
   bool apply;
 
   __device__ __forceinline__ double one(int64_t o) const {
-    double v = __ldg(x + o);
+    double v = ldd<COH>(x + o);
     if constexpr (MODE == kModeOuter) {
-      if (apply) v = dadd(v, (double)to_f(e[o]));
+      if (apply) v = dadd(v, (double)ldf<COH>(e + o));
     }
     return v;
   }
@@ -190,13 +238,13 @@ struct F64Src {
       b = 0.0;
       return;
     }
-    const double2 v = __ldg(reinterpret_cast<const double2*>(x + o));
+    const double2 v = ldd2<COH>(x + o);
     a = v.x;
     b = v.y;
     if constexpr (MODE == kModeOuter) {
       if (apply) {
-        a = dadd(a, (double)to_f(e[o]));
-        b = dadd(b, (double)to_f(e[o + 1]));
+        a = dadd(a, (double)ldf<COH>(e + o));
+        b = dadd(b, (double)ldf<COH>(e + o + 1));
       }
     }
   }
@@ -211,25 +259,58 @@ __device__ __forceinline__ void store_r<__nv_bfloat16>(__nv_bfloat16* p, double 
   *p = __float2bfloat16_rn(__double2float_rn(r));
 }
 
-// ---------------------------------------------------------------------------
-// FP64 kernel: sweep (x' = t / 2d), residual only, or the refinement outer
-// step (x_new = x + e; r = b - A x_new; store x_new, r in low precision).
-// Two points per lane, 64 per warp row.
+template <int DIM>
+__device__ __forceinline__ void push_targets(PushTargets& T, const BlockDev& B, const BlockDev* __restrict__ blocks,
+                                             int y) {
+  const int lo = DIM == 2 ? 2 : 4, hi = lo + 1;
+  T.lo_line = T.hi_line = -1;
+  if (B.nbr[lo] >= 0) {
+    const BlockDev& N = blocks[B.nbr[lo]];
+    const Geo<DIM> GN(N, y);
+    T.lo_line = GN.line(GN.extent);
+  }
+  if (B.nbr[hi] >= 0) {
+    const BlockDev& N = blocks[B.nbr[hi]];
+    const Geo<DIM> GN(N, y);
+    T.hi_line = GN.line(-1);
+  }
+  T.lo_side = T.hi_side = -1;
+  T.lo_side_step = T.hi_side_step = 0;
+  if constexpr (DIM == 3) {
+    if (y == 0 && B.nbr[2] >= 0) {
+      const BlockDev& N = blocks[B.nbr[2]];
+      T.lo_side = N.off + (int64_t)(N.by + 1) * N.pitch;
+      T.lo_side_step = N.plane;
+    }
+    if (y == B.by - 1 && B.nbr[3] >= 0) {
+      const BlockDev& N = blocks[B.nbr[3]];
+      T.hi_side = N.off;
+      T.hi_side_step = N.plane;
+    }
+  }
+  T.w_col = T.e_col = -1;
+  if (B.nbr[0] >= 0) {
+    const BlockDev& N = blocks[B.nbr[0]];
+    T.w_col = N.xoff + (int64_t)N.by * N.bz;  // the west neighbour's east ghost column
+  }
+  if (B.nbr[1] >= 0) T.e_col = blocks[B.nbr[1]].xoff;  // the east neighbour's west column
+}
 
-template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR>
-__global__ void __launch_bounds__(kThreads)
-k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
-      const SolveDev* __restrict__ solves, int epar) {
+// ---------------------------------------------------------------------------
+// FP64 work item: sweep (x' = t / 2d), residual only, or the refinement outer
+// step (x_new = x + e; r = b - A x_new; store x_new, r in low precision).
+// Two points per lane, 64 per warp row.  Every load of line m+1 is issued
+// while line m is computed.
+
+template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, bool COH>
+__device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __restrict__ blocks,
+                                         const SolveDev* __restrict__ solves, int kpar, int epar) {
   constexpr bool WRITE = MODE != kModeResid;
   const int lane = threadIdx.x & 31;
-  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (w >= nitems) return;
-  const WorkItem it = items[w];
   const BlockDev B = blocks[it.block];
   const SolveDev* S = solves + B.solve;
-  if (!S->active) return;
   const int par = (S->phase + kpar) & 1;
-  F64Src<MODE, TE> src;
+  F64Src<MODE, TE, COH> src;
   src.x = S->x[par];
   src.e = MODE == kModeOuter ? reinterpret_cast<const TE*>(S->e[epar]) : nullptr;
   src.apply = MODE == kModeOuter && S->apply_e;
@@ -247,95 +328,91 @@ k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* 
   const bool east_inner = x + 2 < bx;
   const int64_t gW = B.xoff;
   const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
-
   PushTargets T;
-  if constexpr (PUSH && WRITE) {
-    const int lo = DIM == 2 ? 2 : 4, hi = lo + 1;
-    T.lo_line = T.hi_line = -1;
-    if (B.nbr[lo] >= 0) {
-      const BlockDev& N = blocks[B.nbr[lo]];
-      const Geo<DIM> GN(N, y);
-      T.lo_line = GN.line(GN.extent);
-    }
-    if (B.nbr[hi] >= 0) {
-      const BlockDev& N = blocks[B.nbr[hi]];
-      const Geo<DIM> GN(N, y);
-      T.hi_line = GN.line(-1);
-    }
-    T.lo_side = T.hi_side = -1;
-    if constexpr (DIM == 3) {
-      if (y == 0 && B.nbr[2] >= 0) {
-        const BlockDev& N = blocks[B.nbr[2]];
-        T.lo_side = N.off + (int64_t)(N.by + 1) * N.pitch;
-        T.lo_side_step = N.plane;
-      }
-      if (y == B.by - 1 && B.nbr[3] >= 0) {
-        const BlockDev& N = blocks[B.nbr[3]];
-        T.hi_side = N.off;
-        T.hi_side_step = N.plane;
-      }
-    }
-    T.w_col = T.e_col = -1;
-    if (B.nbr[0] >= 0) {
-      const BlockDev& N = blocks[B.nbr[0]];
-      T.w_col = N.xoff + (int64_t)N.by * N.bz;  // the west neighbour's east ghost column
-    }
-    if (B.nbr[1] >= 0) T.e_col = blocks[B.nbr[1]].xoff;  // the east neighbour's west column
-  }
+  if constexpr (PUSH && WRITE) push_targets<DIM>(T, B, blocks, y);
 
   const int m0 = DIM == 2 ? it.y0 : it.z0;
   const int mend = m0 + it.n;
-  int m = m0;
 
-  // lines m-1 (prev) and m (cur)
-  double p0, p1, c0, c1;
-  src.two(G.line(m - 1) + x, v0, p0, p1);
-  src.two(G.line(m) + x, v0, c0, c1);
+  // Values of line m gathered by one lane: the edge scalars it needs (east of
+  // point 1 for lane 31 / the lane holding the block's last point, west of
+  // point 0 for lane 0, the ghost east of point 0 for the lane whose point 0
+  // is last), the source, and in 3D the side rows.
+  // A lane needs at most two edge values: `wv` (lane 0) and one of `eg`
+  // (lane 31 or the lane whose point 1 is last: east of point 1; the lane
+  // whose point 0 is last: its east ghost).
+  struct LineAux {
+    double eg;   // x[m][x+2], or the east ghost of point 1 or of point 0
+    double wv;   // lane 0: x[m][xs-1] or the west ghost
+    double f0, f1;
+    double sn0, sn1;
+  };
+  auto load_aux = [&](int m, LineAux& a) {
+    const int64_t lc = G.line(m);
+    const int col = G.col(m);
+    a.eg = 0.0;
+    a.wv = 0.0;
+    if (lane == 31 && east_inner) a.eg = src.one(lc + x + 2);
+    if (last1 || last0) a.eg = src.one(gE + col);
+    if (lane == 0) a.wv = xs > 0 ? src.one(lc + xs - 1) : src.one(gW + col);
+    a.f0 = 0.0;
+    a.f1 = 0.0;
+    if (v0) {
+      const double2 fv = ldd2<false>(f + lc + x);
+      a.f0 = fv.x;
+      a.f1 = fv.y;
+    }
+    a.sn0 = 0.0;
+    a.sn1 = 0.0;
+    if constexpr (DIM == 3) {
+      double s0, s1, q0, q1;
+      src.two(lc - G.side + x, v0, s0, s1);
+      src.two(lc + G.side + x, v0, q0, q1);
+      a.sn0 = dadd(s0, q0);
+      a.sn1 = dadd(s1, q1);
+    }
+  };
+
+  // lines m-1 (p), m (c), m+1 (n) and the aux values of line m
+  double p0, p1, c0, c1, n0, n1;
+  src.two(G.line(m0 - 1) + x, v0, p0, p1);
+  src.two(G.line(m0) + x, v0, c0, c1);
+  src.two(G.line(m0 + 1) + x, v0, n0, n1);
+  LineAux a;
+  load_aux(m0, a);
   // prologue pairs of line m-1: A0p = P(m-1, x) = p[x+1] + c[x]; A1p = P(m-1, x+1)
   double pE = __shfl_down_sync(FULL_MASK, p0, 1);
-  if (lane == 31 && east_inner) pE = src.one(G.line(m - 1) + x + 2);
+  if (lane == 31 && east_inner) pE = src.one(G.line(m0 - 1) + x + 2);
+  if (last0) c1 = a.eg;
   double A0p = dadd(p1, c0);
   double A1p = dadd(pE, c1);
 
-  for (; m < mend; ++m) {
+  for (int m = m0; m < mend; ++m) {
     const int64_t lc = G.line(m);
     const int col = G.col(m);
-    if (last0) c1 = src.one(gE + col);
-    double n0, n1;
-    src.two(G.line(m + 1) + x, v0, n0, n1);
-    double f0 = 0.0, f1 = 0.0;
-    if (v0) {
-      const double2 fv = __ldg(reinterpret_cast<const double2*>(f + lc + x));
-      f0 = fv.x;
-      f1 = fv.y;
-    }
-    double sn0 = 0.0, sn1 = 0.0;
-    if constexpr (DIM == 3) {
-      double a0, a1, b0_, b1_;
-      src.two(lc - G.side + x, v0, a0, a1);
-      src.two(lc + G.side + x, v0, b0_, b1_);
-      sn0 = dadd(a0, b0_);
-      sn1 = dadd(a1, b1_);
+    // prefetch line m+2 and the aux values of line m+1
+    double nn0 = 0.0, nn1 = 0.0;
+    LineAux an;
+    const bool more = m + 1 < mend;
+    if (more) {
+      src.two(G.line(m + 2) + x, v0, nn0, nn1);
+      load_aux(m + 1, an);
     }
     // east neighbour of point x+1 on line m
     double e1 = __shfl_down_sync(FULL_MASK, c0, 1);
-    if (lane == 31 && east_inner) e1 = src.one(lc + x + 2);
-    if (last1) e1 = src.one(gE + col);
+    if ((lane == 31 && east_inner) || last1) e1 = a.eg;
     // (W + S) pair of point x: from the left lane, or formed here on lane 0
     double bw = __shfl_up_sync(FULL_MASK, A1p, 1);
-    if (lane == 0) {
-      const double wv = xs > 0 ? src.one(lc + xs - 1) : src.one(gW + col);
-      bw = dadd(wv, p0);
-    }
+    if (lane == 0) bw = dadd(a.wv, p0);
     const double A0 = dadd(c1, n0);  // P(m, x)   = c[x+1] + n[x]
     const double A1 = dadd(e1, n1);  // P(m, x+1) = c[x+2] + n[x+1]
     double t0 = dadd(bw, A0), t1 = dadd(A0p, A1);
     if constexpr (DIM == 3) {
-      t0 = dadd(t0, sn0);
-      t1 = dadd(t1, sn1);
+      t0 = dadd(t0, a.sn0);
+      t1 = dadd(t1, a.sn1);
     }
-    t0 = dadd(t0, f0);
-    t1 = dadd(t1, f1);
+    t0 = dadd(t0, a.f0);
+    t1 = dadd(t1, a.f1);
 
     if constexpr (WRITE) {
       double o0, o1;
@@ -405,8 +482,22 @@ k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* 
     p0 = c0;
     p1 = c1;
     c0 = n0;
-    c1 = n1;
+    c1 = last0 ? an.eg : n1;
+    n0 = nn0;
+    n1 = nn1;
+    a = an;
   }
+}
+
+template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads, (DIM == 2 && MODE == kModeSweep) ? 3 : 1)
+k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
+      const SolveDev* __restrict__ solves, int epar) {
+  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (w >= nitems) return;
+  const WorkItem it = items[w];
+  if (!solves[blocks[it.block].solve].active) return;
+  f64_item<DIM, MODE, PUSH, RESID, TE, TR, false>(it, blocks, solves, kpar, epar);
 }
 
 // ---------------------------------------------------------------------------
@@ -415,17 +506,12 @@ k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* 
 // TR.  Four points per lane, 128 per warp row.  FIRST: the input e is zero,
 // so only r is read (e' = (0 + r) / 2d).
 
-template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR>
-__global__ void __launch_bounds__(kThreads)
-k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
-      const SolveDev* __restrict__ solves, int epar) {
+template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR, bool COH>
+__device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __restrict__ blocks,
+                                         const SolveDev* __restrict__ solves, int epar) {
   const int lane = threadIdx.x & 31;
-  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
-  if (w >= nitems) return;
-  const WorkItem it = items[w];
   const BlockDev B = blocks[it.block];
   const SolveDev* S = solves + B.solve;
-  if (!S->active) return;
   const TE* __restrict__ es = reinterpret_cast<const TE*>(S->e[epar ^ 1]);
   TE* __restrict__ ed = reinterpret_cast<TE*>(S->e[epar]);
   const TR* __restrict__ rr = reinterpret_cast<const TR*>(S->r);
@@ -439,41 +525,8 @@ k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict
   const bool any = nvalid > 0;
   const int64_t gW = B.xoff;
   const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
-
   PushTargets T;
-  if constexpr (PUSH) {
-    const int lo = DIM == 2 ? 2 : 4, hi = lo + 1;
-    T.lo_line = T.hi_line = -1;
-    if (B.nbr[lo] >= 0) {
-      const BlockDev& N = blocks[B.nbr[lo]];
-      const Geo<DIM> GN(N, y);
-      T.lo_line = GN.line(GN.extent);
-    }
-    if (B.nbr[hi] >= 0) {
-      const BlockDev& N = blocks[B.nbr[hi]];
-      const Geo<DIM> GN(N, y);
-      T.hi_line = GN.line(-1);
-    }
-    T.lo_side = T.hi_side = -1;
-    if constexpr (DIM == 3) {
-      if (y == 0 && B.nbr[2] >= 0) {
-        const BlockDev& N = blocks[B.nbr[2]];
-        T.lo_side = N.off + (int64_t)(N.by + 1) * N.pitch;
-        T.lo_side_step = N.plane;
-      }
-      if (y == B.by - 1 && B.nbr[3] >= 0) {
-        const BlockDev& N = blocks[B.nbr[3]];
-        T.hi_side = N.off;
-        T.hi_side_step = N.plane;
-      }
-    }
-    T.w_col = T.e_col = -1;
-    if (B.nbr[0] >= 0) {
-      const BlockDev& N = blocks[B.nbr[0]];
-      T.w_col = N.xoff + (int64_t)N.by * N.bz;
-    }
-    if (B.nbr[1] >= 0) T.e_col = blocks[B.nbr[1]].xoff;
-  }
+  if constexpr (PUSH) push_targets<DIM>(T, B, blocks, y);
 
   const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   const int m0 = DIM == 2 ? it.y0 : it.z0;
@@ -481,15 +534,15 @@ k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict
   float4 p = zero4, c = zero4;
   if constexpr (!FIRST) {
     if (any) {
-      p = ld4(es + G.line(m0 - 1) + x);
-      c = ld4(es + G.line(m0) + x);
+      p = ldf4<COH>(es + G.line(m0 - 1) + x);
+      c = ldf4<COH>(es + G.line(m0) + x);
     }
   }
   for (int m = m0; m < mend; ++m) {
     const int64_t lc = G.line(m);
     const int col = G.col(m);
     float4 n = zero4, rv = zero4;
-    if (any) rv = ld4(rr + lc + x);
+    if (any) rv = ldf4<false>(rr + lc + x);  // r is read-only during every sweep
     float4 o;
     if constexpr (FIRST) {
       o.x = jdivf<DIM>(__fadd_rn(0.0f, rv.x));
@@ -497,22 +550,21 @@ k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict
       o.z = jdivf<DIM>(__fadd_rn(0.0f, rv.z));
       o.w = jdivf<DIM>(__fadd_rn(0.0f, rv.w));
     } else {
-      if (any) n = ld4(es + G.line(m + 1) + x);
+      if (any) n = ldf4<COH>(es + G.line(m + 1) + x);
       float4 sa = zero4, sb = zero4;
       if constexpr (DIM == 3) {
         if (any) {
-          sa = ld4(es + lc - G.side + x);
-          sb = ld4(es + lc + G.side + x);
+          sa = ldf4<COH>(es + lc - G.side + x);
+          sb = ldf4<COH>(es + lc + G.side + x);
         }
       }
       // west of point 0, east of point 3
       float wv = __shfl_up_sync(FULL_MASK, c.w, 1);
-      if (lane == 0) wv = xs > 0 ? to_f(es[lc + xs - 1]) : to_f(es[gW + col]);
+      if (lane == 0) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
       float ev = __shfl_down_sync(FULL_MASK, c.x, 1);
-      if (lane == 31 && x + 4 < bx) ev = to_f(es[lc + x + 4]);
-      // the lane holding the block's last point takes the east ghost
+      if (lane == 31 && x + 4 < bx) ev = ldf<COH>(es + lc + x + 4);
       float ge = 0.f;
-      if (any && nvalid <= 4) ge = to_f(es[gE + col]);
+      if (any && nvalid <= 4) ge = ldf<COH>(es + gE + col);
       const float cc[6] = {wv, c.x, c.y, c.z, c.w, ev};
       float ov[4];
 #pragma unroll
@@ -543,6 +595,130 @@ k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict
       c = n;
     }
   }
+}
+
+template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads)
+k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
+      const SolveDev* __restrict__ solves, int epar) {
+  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (w >= nitems) return;
+  const WorkItem it = items[w];
+  if (!solves[blocks[it.block].solve].active) return;
+  low_item<DIM, FIRST, PUSH, TE, TR, false>(it, blocks, solves, epar);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent block scheduler (section 3.1.4's push/pop scheduler and the
+// implicit dependencies of section 3.1.2, moved onto the device).  A task is
+// one CTA's worth of warp items of one block; (sweep j, task t) pairs are
+// handed out in sweep order by an atomic counter.  Before sweep j of block b
+// runs, b and its neighbours must have finished sweep j-1: that covers both
+// the data b reads (its interior and the ghosts its neighbours pushed) and the
+// buffer it overwrites (read by b and its neighbours during sweep j-1).  A task
+// only ever waits for tasks with smaller indices, which were taken earlier by
+// CTAs that are running, so the scheme needs no co-residency guarantee.  Every
+// wait is bounded: when it runs out the task records JACOBI_ERR_TIMEOUT in the
+// control word and every CTA leaves.
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+template <bool LOW>
+__device__ bool wait_deps(const BlockDev& B, int b, const BlockDev* __restrict__ blocks, const uint32_t* done, int j,
+                          SchedCtl* ctl, uint32_t spin_limit, int poison) {
+  for (int k = -1; k < 6; ++k) {
+    const int q = k < 0 ? b : B.nbr[k];
+    if (q < 0) continue;
+    const int nt = k < 0 ? (LOW ? B.ntlo : B.nt64) : (LOW ? blocks[q].ntlo : blocks[q].nt64);
+    const uint32_t need = poison ? 0xffffffffu : (uint32_t)j * (uint32_t)nt;
+    uint32_t iters = 0;
+    while (ld_acquire_u32(done + q) < need) {
+      if (++iters > spin_limit || *(volatile uint32_t*)&ctl->status != 0u) return false;
+      __nanosleep(128);
+    }
+  }
+  return true;
+}
+
+template <bool LOW, typename Body>
+__device__ __forceinline__ void persist_loop(const CtaTask* __restrict__ tasks, int ntasks, int nsweeps,
+                                             const BlockDev* __restrict__ blocks, const SolveDev* __restrict__ solves,
+                                             uint32_t* done, SchedCtl* ctl, uint32_t spin_limit, int poison,
+                                             Body body) {
+  __shared__ int s_idx;
+  __shared__ int s_stop;
+  const int warp = threadIdx.x >> 5;
+  const long long total = (long long)ntasks * nsweeps;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const unsigned idx = atomicAdd(&ctl->head, 1u);
+      s_idx = (int)idx;
+      s_stop = ((long long)idx >= total) || (*(volatile uint32_t*)&ctl->status != 0u);
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int idx = s_idx;
+    const int j = idx / ntasks;
+    const CtaTask T = tasks[idx - j * ntasks];
+    const BlockDev& B = blocks[T.block];
+    const bool act = solves[B.solve].active != 0;
+    if (threadIdx.x == 0 && act && j > 0) {
+      if (!wait_deps<LOW>(B, T.block, blocks, done, j, ctl, spin_limit, poison)) {
+        if (atomicExch(&ctl->status, 1u) == 0u) ctl->fail_task = (uint32_t)idx;
+        s_stop = 1;
+      }
+      __threadfence();
+    }
+    __syncthreads();
+    if (s_stop) break;
+    if (act && warp < T.nw) body(T.w0 + warp, j);
+    __syncthreads();
+    if (threadIdx.x == 0 && act) {
+      __threadfence();
+      atomicAdd(done + T.block, 1u);
+    }
+  }
+}
+
+template <int DIM, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads)
+k_persist_low(const CtaTask* __restrict__ tasks, int ntasks, int nsweeps, const WorkItem* __restrict__ items,
+              const BlockDev* __restrict__ blocks, const SolveDev* __restrict__ solves, uint32_t* done, SchedCtl* ctl,
+              uint32_t spin_limit, int poison) {
+  persist_loop<true>(tasks, ntasks, nsweeps, blocks, solves, done, ctl, spin_limit, poison, [&](int wi, int j) {
+    const WorkItem it = items[wi];
+    if (j == 0) low_item<DIM, true, true, TE, TR, true>(it, blocks, solves, 0);
+    else low_item<DIM, false, true, TE, TR, true>(it, blocks, solves, j & 1);
+  });
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(kThreads)
+k_persist_f64(const CtaTask* __restrict__ tasks, int ntasks, int nsweeps, int resid_last,
+              const WorkItem* __restrict__ items, const BlockDev* __restrict__ blocks,
+              const SolveDev* __restrict__ solves, uint32_t* done, SchedCtl* ctl, uint32_t spin_limit, int poison) {
+  persist_loop<false>(tasks, ntasks, nsweeps, blocks, solves, done, ctl, spin_limit, poison, [&](int wi, int j) {
+    const WorkItem it = items[wi];
+    if (resid_last && j == nsweeps - 1)
+      f64_item<DIM, kModeSweep, true, true, float, float, true>(it, blocks, solves, j & 1, 0);
+    else
+      f64_item<DIM, kModeSweep, true, false, float, float, true>(it, blocks, solves, j & 1, 0);
+  });
+}
+
+__global__ void k_solve_ctl(SolveDev* solves, const int32_t* __restrict__ ctl, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const int32_t c = ctl[i];
+  if (c & 8) return;
+  SolveDev* S = solves + i;
+  if (c & 2) S->phase ^= 1;
+  if (c & 4) S->apply_e = 0;
+  S->active = c & 1;
 }
 
 // ---------------------------------------------------------------------------
@@ -854,6 +1030,58 @@ int launch_ghost_fill(const Tables& t, const double* const* faces_dev, int par, 
 int launch_phase_advance(SolveDev* solves, int nsolves, int dphase, int set_apply_e, void* stream) {
   if (nsolves == 0) return 0;
   k_phase_advance<<<grid_of(nsolves, 256), 256, 0, (cudaStream_t)stream>>>(solves, nsolves, dphase, set_apply_e);
+  return (int)cudaGetLastError();
+}
+
+template <typename K>
+static int persist_grid(K kernel, int total_tasks) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0);
+  const int g = std::max(1, sms * std::max(1, per_sm));
+  return std::min(g, std::max(1, total_tasks));
+}
+
+template <int DIM, typename TE, typename TR>
+static int persist_low_typed(const Tables& t, int nsweeps, cudaStream_t s) {
+  if (t.ntlo == 0 || nsweeps <= 0) return 0;
+  auto k = k_persist_low<DIM, TE, TR>;
+  const int g = persist_grid(k, t.ntlo * nsweeps);
+  k<<<g, kThreads, 0, s>>>(t.tlo, t.ntlo, nsweeps, t.wlo, t.blocks, t.solves, t.done, t.ctl, t.spin_limit, t.poison);
+  return (int)cudaGetLastError();
+}
+
+template <int DIM>
+static int persist_low_dim(const Tables& t, int nsweeps, int low, bool r_bf16, cudaStream_t s) {
+  if (low == kLowF32) return persist_low_typed<DIM, float, float>(t, nsweeps, s);
+  if (r_bf16) return persist_low_typed<DIM, __nv_bfloat16, __nv_bfloat16>(t, nsweeps, s);
+  return persist_low_typed<DIM, __nv_bfloat16, float>(t, nsweeps, s);
+}
+
+int launch_persist_low(const Tables& t, int nsweeps, int low, bool r_bf16, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  return t.ndim == 2 ? persist_low_dim<2>(t, nsweeps, low, r_bf16, s) : persist_low_dim<3>(t, nsweeps, low, r_bf16, s);
+}
+
+template <int DIM>
+static int persist_f64_dim(const Tables& t, int nsweeps, bool resid_last, cudaStream_t s) {
+  if (t.nt64 == 0 || nsweeps <= 0) return 0;
+  auto k = k_persist_f64<DIM>;
+  const int g = persist_grid(k, t.nt64 * nsweeps);
+  k<<<g, kThreads, 0, s>>>(t.t64, t.nt64, nsweeps, resid_last ? 1 : 0, t.w64, t.blocks, t.solves, t.done, t.ctl,
+                           t.spin_limit, t.poison);
+  return (int)cudaGetLastError();
+}
+
+int launch_persist_f64(const Tables& t, int nsweeps, bool resid_last, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  return t.ndim == 2 ? persist_f64_dim<2>(t, nsweeps, resid_last, s) : persist_f64_dim<3>(t, nsweeps, resid_last, s);
+}
+
+int launch_solve_ctl(SolveDev* solves, const int32_t* ctl, int nsolves, void* stream) {
+  if (nsolves == 0) return 0;
+  k_solve_ctl<<<grid_of(nsolves, 256), 256, 0, (cudaStream_t)stream>>>(solves, ctl, nsolves);
   return (int)cudaGetLastError();
 }
 

@@ -17,8 +17,8 @@ import numpy as np
 
 from . import build as _build
 
-F64, F32_REFINE, BF16_REFINE = 0, 1, 2
-DTYPES = {"f64": F64, "f32_refine": F32_REFINE, "bf16_refine": BF16_REFINE}
+F64, F32_REFINE, BF16_REFINE, BF16_REFINE_R16 = 0, 1, 2, 3
+DTYPES = {"f64": F64, "f32_refine": F32_REFINE, "bf16_refine": BF16_REFINE, "bf16r16_refine": BF16_REFINE_R16}
 BC_ZERO, BC_CONST, BC_FACES = 0, 1, 2
 
 STATUS = {0: "OK", 1: "ERR_INVALID", 2: "ERR_OOM", 3: "ERR_CUDA", 4: "ERR_NOT_CONVERGED",
@@ -29,7 +29,8 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT
 EXPORTS = ["jacobi_set_allocator", "jacobi_create", "jacobi_sweep", "jacobi_residual", "jacobi_solve",
            "jacobi_get_field", "jacobi_set_field", "jacobi_set_source", "jacobi_set_option",
            "jacobi_get_option", "jacobi_profile", "jacobi_device_bytes", "jacobi_destroy",
-           "jacobi_last_error", "jacobi_version", "jacobi_residual_noalloc"]
+           "jacobi_last_error", "jacobi_version", "jacobi_residual_noalloc",
+           "jacobi_batch_create", "jacobi_batch_solve", "jacobi_batch_get_field"]
 
 
 class JacobiError(RuntimeError):
@@ -40,6 +41,16 @@ class JacobiError(RuntimeError):
 
 class Boundary(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("value", ctypes.c_double), ("faces", ctypes.c_void_p * 6)]
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("block", ctypes.c_int64 * 3),
+                ("bc", Boundary), ("source", ctypes.c_void_p), ("x0", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reserved", ctypes.c_int32), ("sweeps", ctypes.c_int64),
+                ("rel", ctypes.c_double), ("seconds", ctypes.c_double)]
 
 
 _lib = None
@@ -82,6 +93,10 @@ def load(path: str | None = None):
         "jacobi_last_error": (ctypes.c_char_p, [vp]),
         "jacobi_version": (ctypes.c_int, []),
         "jacobi_residual_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, vp, vp, ctypes.POINTER(vp), vp, vp]),
+        "jacobi_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(Problem),
+                                                ctypes.c_int, vp]),
+        "jacobi_batch_solve": (ctypes.c_int, [vp, ctypes.c_double, i64, ctypes.POINTER(Result)]),
+        "jacobi_batch_get_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -234,6 +249,25 @@ def jacobi_residual_noalloc(ndim, dims, x_ptr, f_ptr, face_ptrs, rss_ptr, stream
     return _check(load().jacobi_residual_noalloc(int(ndim), d, x_ptr, f_ptr, fp, rss_ptr, stream), None)
 
 
+def jacobi_batch_create(problems, dtype, stream=None):
+    """problems: a ctypes array of Problem."""
+    h = ctypes.c_void_p()
+    _check(load().jacobi_batch_create(ctypes.byref(h), len(problems), problems, int(dtype), stream), None)
+    return h
+
+
+def jacobi_batch_solve(h, tol, max_sweeps, n):
+    res = (Result * n)()
+    st = load().jacobi_batch_solve(h, float(tol), int(max_sweeps), res)
+    if st not in (OK, ERR_NOT_CONVERGED, ERR_DIVERGED):
+        _check(st, h)
+    return st, res
+
+
+def jacobi_batch_get_field(h, i, out_ptr, on_device):
+    return _check(load().jacobi_batch_get_field(h, int(i), out_ptr, int(on_device)), h)
+
+
 def jacobi_last_error(h=None):
     m = load().jacobi_last_error(h)
     return m.decode() if m else ""
@@ -322,6 +356,81 @@ class Solver:
 
     def device_bytes(self):
         return jacobi_device_bytes(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            jacobi_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        if not sys.is_finalizing():
+            try:
+                self.close()
+            except Exception:  # noqa: BLE001
+                pass
+
+
+class Batch:
+    """Many independent grids in one context: Batch(problems, dtype=...) where
+    each problem has .dims, .block, .faces, .source, .x0 (host numpy)."""
+
+    def __init__(self, problems, dtype="f32_refine", stream=None, torch_alloc=True, **options):
+        self.n = len(problems)
+        self.shapes = [tuple(reversed(tuple(p.dims))) for p in problems]
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        if torch_alloc:
+            use_torch_allocator(True)
+        arr = (Problem * self.n)()
+        keep = []
+        for i, p in enumerate(problems):
+            dims = list(p.dims)
+            blk = list(p.block)
+            arr[i].ndim = len(dims)
+            for a in range(3):
+                arr[i].dims[a] = dims[a] if a < len(dims) else 1
+                arr[i].block[a] = blk[a] if a < len(blk) else 1
+            bc, k = make_boundary(p.faces)
+            keep.append(k)
+            arr[i].bc = bc
+            for name in ("source", "x0"):
+                v = getattr(p, name)
+                if v is None:
+                    setattr(arr[i], name, None)
+                else:
+                    a_ = np.ascontiguousarray(v, dtype=np.float64)
+                    keep.append(a_)
+                    setattr(arr[i], name, a_.ctypes.data)
+        self.stream = default_stream() if stream is None else stream
+        self.h = jacobi_batch_create(arr, self.dtype, self.stream)
+        del keep
+        for k, v in options.items():
+            jacobi_set_option(self.h, k, v)
+
+    def solve(self, tol, max_sweeps):
+        st, res = jacobi_batch_solve(self.h, tol, max_sweeps, self.n)
+        return st, [(r.status, r.sweeps, r.rel, r.seconds) for r in res]
+
+    def sweep(self, n):
+        jacobi_sweep(self.h, n)
+
+    def field(self, i, out=None):
+        if out is None:
+            out = np.empty(self.shapes[i], dtype=np.float64)
+        p, dev = _ptr(out)
+        jacobi_batch_get_field(self.h, i, p, dev)
+        return out
+
+    def set_option(self, key, value):
+        jacobi_set_option(self.h, key, value)
+
+    def profile(self, kernel, reset=False):
+        return jacobi_profile(self.h, kernel, reset)
 
     def close(self):
         if getattr(self, "h", None):
