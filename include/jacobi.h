@@ -225,6 +225,55 @@ jacobi_status jacobi_batch_solve(jacobi_t ctx, double tol, int64_t max_sweeps, j
 /* Copy grid i's current iterate out (interior-dense, host or device memory). */
 jacobi_status jacobi_batch_get_field(jacobi_t ctx, int i, double* out, int on_device);
 
+/* ---- serving: continuous batching under an HBM budget -------------------- */
+
+typedef struct jacobi_server* jacobi_server_t;
+
+typedef struct {
+  int64_t submitted, admitted, completed, rejected; /* request counts */
+  int64_t active, queued;                           /* solves on the GPU / waiting now */
+  int64_t bytes_in_use, budget_bytes;               /* device memory of the arena */
+  int64_t steps;                                    /* refinement steps run */
+  double lups;                                      /* lattice-point updates of completed solves */
+} jacobi_server_stats;
+
+/* Start a server: one arena of hbm_budget_bytes of device memory (allocated
+ * here, through the registered allocator; the paper's custom device pool of
+ * section 4.1.2) and a driver thread that owns all GPU work (section 4.1.6's
+ * dedicated per-device thread).  dtype is a refinement dtype (1..3);
+ * max_slots bounds the solves resident at once per dimensionality.  All
+ * solves run refinement steps of "refine_period" inner sweeps (option, set
+ * before the first submit; default 20) with the persistent scheduler. */
+jacobi_status jacobi_server_create(jacobi_server_t* out, int dtype, int64_t hbm_budget_bytes, int max_slots,
+                                   void* cuda_stream);
+
+/* Options "refine_period", "schedule", "graph", "halo", "rows_low", "rows_f64"
+ * (meaning as for contexts); JACOBI_ERR_BUSY once a request was submitted. */
+jacobi_status jacobi_server_set_option(jacobi_server_t srv, const char* key, int64_t value);
+
+/* Queue one solve to relative residual tol (inputs are copied; thread-safe).
+ * The driver admits queued requests in arrival order while their device
+ * memory fits in the arena, keeps their state resident, steps every active
+ * solve together and retires each as soon as it passes (continuous batching).
+ * A solve's result equals the single-grid jacobi_solve with the same
+ * refine_period when max_sweeps is a multiple of refine_period.
+ * JACOBI_ERR_BUSY: the request can never fit in the budget. */
+jacobi_status jacobi_server_submit(jacobi_server_t srv, const jacobi_problem* p, double tol, int64_t max_sweeps,
+                                   uint64_t* ticket);
+
+/* JACOBI_OK and the result (and, if field_out is not NULL, the interior-dense
+ * field in host memory) when the request is done -- the ticket is then
+ * forgotten; JACOBI_ERR_BUSY while it is queued or running. */
+jacobi_status jacobi_server_poll(jacobi_server_t srv, uint64_t ticket, jacobi_result* out, double* field_out);
+
+/* Block until the ticket is done or timeout_s elapses (JACOBI_ERR_BUSY). */
+jacobi_status jacobi_server_wait(jacobi_server_t srv, uint64_t ticket, double timeout_s);
+
+jacobi_status jacobi_server_get_stats(jacobi_server_t srv, jacobi_server_stats* out);
+
+/* Stops the driver thread and frees everything (pending requests are dropped). */
+void jacobi_server_destroy(jacobi_server_t srv);
+
 /* Residual of an interior-dense field WITHOUT ANY DEVICE ALLOCATION.
  *
  * The paper has no counterpart to this call; it exists for callers that

@@ -159,9 +159,9 @@ int64_t solve_device_bytes(const ProblemSpec& p, int dtype, bool r_bf16) {
 // ---------------------------------------------------------------------------
 // workset
 
-Workset::Workset(int ndim, int dtype, cudaStream_t stream, int capacity, bool r_bf16)
+Workset::Workset(int ndim, int dtype, cudaStream_t stream, int capacity, bool r_bf16, const AllocHooks* hooks)
     : ndim_(ndim), dtype_(dtype), capacity_(capacity), r_bf16_(r_bf16 || dtype == 3), stream_(stream),
-      cur_(stream), pool_(current_alloc_hooks(), stream) {
+      cur_(stream), pool_(hooks ? *hooks : current_alloc_hooks(), stream) {
   solves_.assign(capacity, nullptr);
   d_solves_ = (SolveDev*)pool_.alloc(sizeof(SolveDev) * capacity);
   d_rss_ = (double*)pool_.alloc(sizeof(double) * capacity);

@@ -124,7 +124,8 @@ struct SlotResult {
 
 class Workset {
  public:
-  Workset(int ndim, int dtype, cudaStream_t stream, int capacity, bool r_bf16 = false);
+  Workset(int ndim, int dtype, cudaStream_t stream, int capacity, bool r_bf16 = false,
+          const AllocHooks* hooks = nullptr);
   ~Workset();
 
   // Adds a solve, uploads its inputs, computes ||b||; returns its slot.
@@ -153,6 +154,10 @@ class Workset {
   void solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>& res);
   // Pick rows_f64 / rows_low / schedule by timing (restores the state).
   void autotune();
+  // Serving: k inner sweeps then the outer step for every active solve (a
+  // newly added solve's first inner sweeps see r = 0 and leave e = 0, so its
+  // first outer step only computes r of its initial iterate).
+  void serve_step(int64_t k);
 
   void scatter(int slot, const double* dense, int which, int on_device);
   void gather(int slot, double* dense, int on_device);

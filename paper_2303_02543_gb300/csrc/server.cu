@@ -1,0 +1,483 @@
+// Serving loop: continuous batching of Jacobi solves under an HBM budget.
+//
+// Requests arrive through jacobi_server_submit from any thread.  One driver
+// thread per server (the dedicated per-device thread of section 4.1.6) owns
+// the GPU work: between refinement steps it retires finished solves (copying
+// their fields to host memory and freeing their state) and admits queued
+// requests while their device memory fits in the budget.  Every admitted
+// solve's state stays resident until it finishes; all active solves of one
+// dimensionality advance together in the same launches.
+//
+// Device memory comes from one arena allocated at creation (the custom
+// device memory pool of section 4.1.2): the driver thread never calls an
+// allocator outside the library, and admission is exact.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <cmath>
+#include <thread>
+
+#include "../../include/jacobi.h"
+#include "engine.h"
+
+using namespace jgb;
+
+namespace jgb {
+void set_thread_error(const std::string& msg);
+}
+
+namespace {
+
+// First-fit arena over one device allocation, 256-byte granules.
+class Arena {
+ public:
+  bool init(size_t bytes, const AllocHooks& hooks, cudaStream_t s) {
+    hooks_ = hooks;
+    stream_ = s;
+    size_ = (bytes + 255) & ~(size_t)255;
+    if (hooks_.alloc) base_ = (char*)hooks_.alloc(size_, (void*)s, hooks_.user);
+    else if (cudaMalloc((void**)&base_, size_) != cudaSuccess) base_ = nullptr;
+    if (!base_) {
+      cudaGetLastError();
+      return false;
+    }
+    free_[0] = size_;
+    return true;
+  }
+  ~Arena() {
+    if (!base_) return;
+    cudaStreamSynchronize(stream_);
+    if (hooks_.free) hooks_.free(base_, (void*)stream_, hooks_.user);
+    else cudaFree(base_);
+  }
+  void* alloc(size_t n) {
+    std::lock_guard<std::mutex> lk(mu_);
+    n = (n + 255) & ~(size_t)255;
+    for (auto it = free_.begin(); it != free_.end(); ++it) {
+      if (it->second < n) continue;
+      const size_t off = it->first, sz = it->second;
+      free_.erase(it);
+      if (sz > n) free_[off + n] = sz - n;
+      used_[off] = n;
+      in_use_ += n;
+      return base_ + off;
+    }
+    return nullptr;
+  }
+  void release(void* p) {
+    std::lock_guard<std::mutex> lk(mu_);
+    const size_t off = (size_t)((char*)p - base_);
+    auto u = used_.find(off);
+    if (u == used_.end()) return;
+    size_t n = u->second, start = off;
+    used_.erase(u);
+    in_use_ -= n;
+    auto nx = free_.lower_bound(off);
+    if (nx != free_.end() && nx->first == off + n) {
+      n += nx->second;
+      free_.erase(nx);
+    }
+    auto pv = free_.lower_bound(off);
+    if (pv != free_.begin()) {
+      --pv;
+      if (pv->first + pv->second == off) {
+        start = pv->first;
+        n += pv->second;
+        free_.erase(pv);
+      }
+    }
+    free_[start] = n;
+  }
+  size_t in_use() const { return in_use_; }
+  size_t size() const { return size_; }
+
+  static void* hook_alloc(size_t n, void*, void* user) { return ((Arena*)user)->alloc(n); }
+  static void hook_free(void* p, void*, void* user) { ((Arena*)user)->release(p); }
+
+ private:
+  AllocHooks hooks_;
+  cudaStream_t stream_ = nullptr;
+  char* base_ = nullptr;
+  size_t size_ = 0, in_use_ = 0;
+  std::map<size_t, size_t> free_, used_;
+  std::mutex mu_;
+};
+
+struct Request {
+  uint64_t ticket = 0;
+  ProblemSpec spec;
+  std::vector<double> faces[6], source, x0;
+  double tol = 1e-8;
+  int64_t max_sweeps = 0;
+  int64_t bytes = 0;
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Active {
+  uint64_t ticket = 0;
+  int64_t sweeps = 0;
+  bool had_outer = false;
+  double tol = 1e-8;
+  int64_t max_sweeps = 0;
+  int64_t points = 0;
+  std::chrono::steady_clock::time_point t_submit;
+};
+
+struct Done {
+  jacobi_result res;
+  std::vector<double> field;
+};
+
+}  // namespace
+
+struct jacobi_server {
+  int dtype = 1;
+  int device = 0;
+  int max_slots = 64;
+  cudaStream_t stream = nullptr;
+  Options opt;
+  Arena arena;
+  Workset* ws[2] = {nullptr, nullptr};  // 2D, 3D
+  std::map<int, Active> active[2];      // slot -> solve
+  std::deque<Request> queue;
+  std::map<uint64_t, Done> done;
+  uint64_t next_ticket = 1;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread driver;
+  bool stop = false;
+  std::string fatal;                    // set when the driver thread fails
+  jacobi_server_stats stats;
+  std::string err;
+
+  ~jacobi_server() {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      stop = true;
+    }
+    cv.notify_all();
+    if (driver.joinable()) driver.join();
+    delete ws[0];
+    delete ws[1];
+  }
+
+  Workset* workset(int ndim) {
+    Workset*& w = ws[ndim - 2];
+    if (!w) {
+      AllocHooks h;
+      h.alloc = &Arena::hook_alloc;
+      h.free = &Arena::hook_free;
+      h.user = &arena;
+      w = new Workset(ndim, dtype, stream, max_slots, dtype == 3, &h);
+      w->opt = opt;
+    }
+    return w;
+  }
+
+  void loop();
+  bool step_once();
+};
+
+// One pass of the driver: admit, step every workset once, retire.
+bool jacobi_server::step_once() {
+  // admission: first fit, in arrival order, within the arena
+  std::vector<Request> admit;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    int free_slots[2] = {max_slots - (int)active[0].size(), max_slots - (int)active[1].size()};
+    int64_t room = (int64_t)arena.size() - (int64_t)arena.in_use();
+    for (auto it = queue.begin(); it != queue.end();) {
+      const int d = it->spec.ndim - 2;
+      // a workset not yet created also needs its tables; keep 1/16 of the request as margin
+      const int64_t need = it->bytes + it->bytes / 16 + (ws[d] ? 0 : (int64_t)(1 << 20));
+      if (free_slots[d] > 0 && need <= room) {
+        room -= need;
+        --free_slots[d];
+        admit.push_back(std::move(*it));
+        it = queue.erase(it);
+      } else {
+        ++it;
+      }
+    }
+  }
+  for (size_t ai = 0; ai < admit.size(); ++ai) {
+    Request& r = admit[ai];
+    const int d = r.spec.ndim - 2;
+    try {
+      Workset* w = workset(r.spec.ndim);
+      const int slot = w->add_solve(r.spec);
+      Active a;
+      a.ticket = r.ticket;
+      a.tol = r.tol;
+      a.max_sweeps = r.max_sweeps;
+      a.points = r.spec.n[0] * r.spec.n[1] * r.spec.n[2];
+      a.t_submit = r.t_submit;
+      active[d][slot] = a;
+      std::lock_guard<std::mutex> lk(mu);
+      stats.admitted += 1;
+    } catch (const JErr& e) {
+      if (e.code == JACOBI_ERR_OOM || e.code == JACOBI_ERR_BUSY) {
+        // fragmentation: this request and the ones after it go back to the
+        // head of the queue, in order, and wait for a retirement
+        std::lock_guard<std::mutex> lk(mu);
+        for (size_t bi = admit.size(); bi-- > ai;) queue.push_front(std::move(admit[bi]));
+        break;
+      }
+      throw;
+    }
+  }
+  bool worked = false;
+  for (int d = 0; d < 2; ++d) {
+    if (active[d].empty()) continue;
+    Workset* w = ws[d];
+    worked = true;
+    const int64_t k = w->opt.refine_period;
+    w->serve_step(k);
+    std::vector<double> rss;
+    w->read_rss(rss);
+    const auto now = std::chrono::steady_clock::now();
+    std::vector<int> finished;
+    for (auto& kv : active[d]) {
+      Active& a = kv.second;
+      if (a.had_outer) a.sweeps += k;
+      a.had_outer = true;
+      const SolveHost* s = w->solve(kv.first);
+      const double rel = s->bss > 0.0 ? std::sqrt(rss[kv.first]) / std::sqrt(s->bss) : std::sqrt(rss[kv.first]);
+      int st = -1;
+      if (!std::isfinite(rel)) st = JACOBI_ERR_DIVERGED;
+      else if (rel <= a.tol) st = JACOBI_OK;
+      else if (a.sweeps >= a.max_sweeps) st = JACOBI_ERR_NOT_CONVERGED;
+      if (st < 0) continue;
+      Done dn;
+      dn.res.status = st;
+      dn.res.reserved = 0;
+      dn.res.sweeps = a.sweeps;
+      dn.res.rel = rel;
+      dn.res.seconds = std::chrono::duration<double>(now - a.t_submit).count();
+      dn.field.resize((size_t)a.points);
+      w->gather(kv.first, dn.field.data(), 0);
+      {
+        std::lock_guard<std::mutex> lk(mu);
+        stats.completed += 1;
+        stats.lups += (double)a.points * (double)a.sweeps;
+        done[a.ticket] = std::move(dn);
+      }
+      finished.push_back(kv.first);
+    }
+    for (int slot : finished) {
+      w->remove_solve(slot);
+      active[d].erase(slot);
+    }
+  }
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    stats.active = (int64_t)(active[0].size() + active[1].size());
+    stats.queued = (int64_t)queue.size();
+    stats.bytes_in_use = (int64_t)arena.in_use();
+    if (worked) stats.steps += 1;
+  }
+  cv.notify_all();
+  return worked || !admit.empty();
+}
+
+void jacobi_server::loop() {
+  cudaSetDevice(device);
+  try {
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        if (stop) break;
+      }
+      const bool worked = step_once();
+      if (!worked) {
+        std::unique_lock<std::mutex> lk(mu);
+        if (stop) break;
+        cv.wait_for(lk, std::chrono::milliseconds(2), [&] { return stop || !queue.empty(); });
+      }
+    }
+  } catch (const JErr& e) {
+    std::lock_guard<std::mutex> lk(mu);
+    fatal = e.msg;
+  } catch (...) {
+    std::lock_guard<std::mutex> lk(mu);
+    fatal = "unexpected internal error in the driver thread";
+  }
+  cv.notify_all();
+}
+
+// Workset::serve_step lives here to keep the serving logic in one file.
+namespace jgb {
+void Workset::serve_step(int64_t k) {
+  if (live() == 0) return;
+  step_refine(k);
+}
+}  // namespace jgb
+
+#define SRV_BEGIN try {
+#define SRV_END(srv)                                   \
+  }                                                    \
+  catch (const JErr& e) {                              \
+    if (srv) (srv)->err = e.msg;                       \
+    set_thread_error(e.msg);                           \
+    return (jacobi_status)e.code;                      \
+  }                                                    \
+  catch (const std::bad_alloc&) {                      \
+    set_thread_error("host allocation failed");        \
+    return JACOBI_ERR_OOM;                             \
+  }                                                    \
+  catch (...) {                                        \
+    set_thread_error("unexpected internal error");     \
+    return JACOBI_ERR_INVALID;                         \
+  }
+
+extern "C" {
+
+jacobi_status jacobi_server_create(jacobi_server_t* out, int dtype, int64_t hbm_budget_bytes, int max_slots,
+                                   void* cuda_stream) {
+  jacobi_server* srv = nullptr;
+  SRV_BEGIN
+  if (!out) throw JErr{JACOBI_ERR_INVALID, "out is NULL"};
+  *out = nullptr;
+  if (dtype < 1 || dtype > 3) throw JErr{JACOBI_ERR_INVALID, "the server runs the refinement dtypes (1..3)"};
+  if (hbm_budget_bytes < (1 << 20)) throw JErr{JACOBI_ERR_INVALID, "hbm_budget_bytes must be >= 1 MiB"};
+  if (max_slots < 1 || max_slots > 4096) throw JErr{JACOBI_ERR_INVALID, "max_slots must be in [1, 4096]"};
+  srv = new jacobi_server();
+  srv->dtype = dtype;
+  srv->max_slots = max_slots;
+  srv->stream = (cudaStream_t)cuda_stream;
+  srv->opt.schedule = 1;
+  memset(&srv->stats, 0, sizeof(srv->stats));
+  cudaGetDevice(&srv->device);
+  if (!srv->arena.init((size_t)hbm_budget_bytes, current_alloc_hooks(), srv->stream)) {
+    delete srv;
+    srv = nullptr;
+    throw JErr{JACOBI_ERR_OOM, "could not allocate the HBM budget"};
+  }
+  srv->driver = std::thread([srv] { srv->loop(); });
+  *out = srv;
+  return JACOBI_OK;
+  SRV_END(srv)
+}
+
+jacobi_status jacobi_server_set_option(jacobi_server_t srv, const char* key, int64_t value) {
+  if (!srv || !key) return JACOBI_ERR_INVALID;
+  SRV_BEGIN
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (srv->ws[0] || srv->ws[1] || !srv->queue.empty())
+    throw JErr{JACOBI_ERR_BUSY, "options are fixed once the first request is submitted"};
+  const std::string k(key);
+  if (k == "refine_period") {
+    if (value < 1 || value > 4096) throw JErr{JACOBI_ERR_INVALID, "refine_period must be in [1, 4096]"};
+    srv->opt.refine_period = value;
+  } else if (k == "schedule" || k == "graph" || k == "halo") {
+    if (value != 0 && value != 1) throw JErr{JACOBI_ERR_INVALID, k + " must be 0 or 1"};
+    (k == "schedule" ? srv->opt.schedule : k == "graph" ? srv->opt.graph : srv->opt.halo) = value;
+  } else if (k == "rows_low" || k == "rows_f64") {
+    if (value < 1) throw JErr{JACOBI_ERR_INVALID, k + " must be >= 1"};
+    (k == "rows_low" ? srv->opt.rows_low : srv->opt.rows_f64) = value;
+  } else {
+    throw JErr{JACOBI_ERR_INVALID, "unknown server option " + k};
+  }
+  return JACOBI_OK;
+  SRV_END(srv)
+}
+
+jacobi_status jacobi_server_submit(jacobi_server_t srv, const jacobi_problem* p, double tol, int64_t max_sweeps,
+                                   uint64_t* ticket) {
+  if (!srv || !p || !ticket) return JACOBI_ERR_INVALID;
+  SRV_BEGIN
+  if (!(tol > 0.0)) throw JErr{JACOBI_ERR_INVALID, "tol must be > 0"};
+  if (max_sweeps < 0) throw JErr{JACOBI_ERR_INVALID, "max_sweeps must be >= 0"};
+  if (p->ndim != 2 && p->ndim != 3) throw JErr{JACOBI_ERR_INVALID, "ndim must be 2 or 3"};
+  Request r;
+  ProblemSpec& s = r.spec;
+  s.ndim = p->ndim;
+  int64_t pts = 1;
+  for (int a = 0; a < 3; ++a) {
+    s.n[a] = a < p->ndim ? p->dims[a] : 1;
+    s.blk[a] = a < p->ndim ? p->block[a] : 1;
+    if (s.n[a] < 1 || s.blk[a] < 1 || s.blk[a] > s.n[a] || s.n[a] >= (1LL << 30))
+      throw JErr{JACOBI_ERR_INVALID, "bad dims/block"};
+    pts *= s.n[a];
+  }
+  s.bc_kind = p->bc.kind;
+  s.bc_value = p->bc.value;
+  if (s.bc_kind < 0 || s.bc_kind > 2) throw JErr{JACOBI_ERR_INVALID, "unknown boundary kind"};
+  // copy the inputs: the caller keeps ownership of its arrays
+  const int64_t fc[6] = {s.n[1] * s.n[2], s.n[1] * s.n[2], s.n[0] * s.n[2],
+                         s.n[0] * s.n[2], s.n[0] * s.n[1], s.n[0] * s.n[1]};
+  if (s.bc_kind == 2)
+    for (int q = 0; q < 2 * p->ndim; ++q)
+      if (p->bc.faces[q]) {
+        r.faces[q].assign(p->bc.faces[q], p->bc.faces[q] + fc[q]);
+        s.faces[q] = r.faces[q].data();
+      }
+  if (p->source) {
+    r.source.assign(p->source, p->source + pts);
+    s.source = r.source.data();
+  }
+  if (p->x0) {
+    r.x0.assign(p->x0, p->x0 + pts);
+    s.x0 = r.x0.data();
+  }
+  r.tol = tol;
+  r.max_sweeps = max_sweeps;
+  r.bytes = solve_device_bytes(s, srv->dtype, srv->dtype == 3);
+  r.t_submit = std::chrono::steady_clock::now();
+  std::lock_guard<std::mutex> lk(srv->mu);
+  if (!srv->fatal.empty()) throw JErr{JACOBI_ERR_CUDA, "server stopped: " + srv->fatal};
+  if (r.bytes + r.bytes / 16 + (1 << 20) > (int64_t)srv->arena.size()) {
+    srv->stats.rejected += 1;
+    throw JErr{JACOBI_ERR_BUSY, "the request needs " + std::to_string(r.bytes) +
+                                    " bytes of device memory, more than the whole budget"};
+  }
+  r.ticket = srv->next_ticket++;
+  *ticket = r.ticket;
+  srv->stats.submitted += 1;
+  srv->queue.push_back(std::move(r));
+  srv->cv.notify_all();
+  return JACOBI_OK;
+  SRV_END(srv)
+}
+
+jacobi_status jacobi_server_poll(jacobi_server_t srv, uint64_t ticket, jacobi_result* out, double* field_out) {
+  if (!srv) return JACOBI_ERR_INVALID;
+  SRV_BEGIN
+  std::lock_guard<std::mutex> lk(srv->mu);
+  auto it = srv->done.find(ticket);
+  if (it == srv->done.end()) {
+    if (!srv->fatal.empty()) throw JErr{JACOBI_ERR_CUDA, "server stopped: " + srv->fatal};
+    if (ticket == 0 || ticket >= srv->next_ticket) throw JErr{JACOBI_ERR_INVALID, "unknown ticket"};
+    return JACOBI_ERR_BUSY;
+  }
+  if (out) *out = it->second.res;
+  if (field_out) memcpy(field_out, it->second.field.data(), it->second.field.size() * sizeof(double));
+  srv->done.erase(it);
+  return JACOBI_OK;
+  SRV_END(srv)
+}
+
+jacobi_status jacobi_server_wait(jacobi_server_t srv, uint64_t ticket, double timeout_s) {
+  if (!srv) return JACOBI_ERR_INVALID;
+  std::unique_lock<std::mutex> lk(srv->mu);
+  const bool ok = srv->cv.wait_for(lk, std::chrono::duration<double>(timeout_s), [&] {
+    return srv->done.count(ticket) > 0 || !srv->fatal.empty();
+  });
+  if (!srv->fatal.empty()) return JACOBI_ERR_CUDA;
+  return ok ? JACOBI_OK : JACOBI_ERR_BUSY;
+}
+
+jacobi_status jacobi_server_get_stats(jacobi_server_t srv, jacobi_server_stats* out) {
+  if (!srv || !out) return JACOBI_ERR_INVALID;
+  std::lock_guard<std::mutex> lk(srv->mu);
+  *out = srv->stats;
+  out->budget_bytes = (int64_t)srv->arena.size();
+  return srv->fatal.empty() ? JACOBI_OK : JACOBI_ERR_CUDA;
+}
+
+void jacobi_server_destroy(jacobi_server_t srv) { delete srv; }
+
+}  // extern "C"

@@ -158,7 +158,8 @@ def batched_2d(seed=2307, count=256, lo=64, hi=2048, block=128, size_scale=1.0):
     for i in range(count):
         nx = max(1, int(round(sx[i] * size_scale)))
         ny = max(1, int(round(sy[i] * size_scale)))
-        probs.append(make_problem((nx, ny), (block, block), seed * 1000003 + i,
+        # a grid narrower than a block is a single block along that axis
+        probs.append(make_problem((nx, ny), (min(block, nx), min(block, ny)), seed * 1000003 + i,
                                   boundary="uniform", source="normal", x0="zero"))
     return probs
 
@@ -185,10 +186,12 @@ def serving_stream(seed=2308, rate=10.0, window_s=60.0, lo2=128, hi2=4096, lo3=3
             break
         if u_kind[i] < 0.5:
             side = int(round(math.exp(math.log(lo2) + u_side[i] * (math.log(hi2) - math.log(lo2)))))
-            dims, block = (side, side), (block2, block2)
+            b = min(block2, side)
+            dims, block = (side, side), (b, b)
         else:
             side = int(round(math.exp(math.log(lo3) + u_side[i] * (math.log(hi3) - math.log(lo3)))))
-            dims, block = (side, side, side), (block3, block3, block3)
+            b = min(block3, side)
+            dims, block = (side, side, side), (b, b, b)
         p = make_problem(dims, block, seed * 1000003 + i, boundary="uniform", source="normal", x0="zero")
         p.meta["arrival"] = t
         out.append(Arrival(t, p))

@@ -30,7 +30,9 @@ EXPORTS = ["jacobi_set_allocator", "jacobi_create", "jacobi_sweep", "jacobi_resi
            "jacobi_get_field", "jacobi_set_field", "jacobi_set_source", "jacobi_set_option",
            "jacobi_get_option", "jacobi_profile", "jacobi_device_bytes", "jacobi_destroy",
            "jacobi_last_error", "jacobi_version", "jacobi_residual_noalloc",
-           "jacobi_batch_create", "jacobi_batch_solve", "jacobi_batch_get_field"]
+           "jacobi_batch_create", "jacobi_batch_solve", "jacobi_batch_get_field",
+           "jacobi_server_create", "jacobi_server_set_option", "jacobi_server_submit", "jacobi_server_poll",
+           "jacobi_server_wait", "jacobi_server_get_stats", "jacobi_server_destroy"]
 
 
 class JacobiError(RuntimeError):
@@ -46,6 +48,11 @@ class Boundary(ctypes.Structure):
 class Problem(ctypes.Structure):
     _fields_ = [("ndim", ctypes.c_int), ("dims", ctypes.c_int64 * 3), ("block", ctypes.c_int64 * 3),
                 ("bc", Boundary), ("source", ctypes.c_void_p), ("x0", ctypes.c_void_p)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "rejected", "active", "queued",
+                                              "bytes_in_use", "budget_bytes", "steps")] + [("lups", ctypes.c_double)]
 
 
 class Result(ctypes.Structure):
@@ -97,6 +104,14 @@ def load(path: str | None = None):
                                                 ctypes.c_int, vp]),
         "jacobi_batch_solve": (ctypes.c_int, [vp, ctypes.c_double, i64, ctypes.POINTER(Result)]),
         "jacobi_batch_get_field": (ctypes.c_int, [vp, ctypes.c_int, vp, ctypes.c_int]),
+        "jacobi_server_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, i64, ctypes.c_int, vp]),
+        "jacobi_server_set_option": (ctypes.c_int, [vp, ctypes.c_char_p, i64]),
+        "jacobi_server_submit": (ctypes.c_int, [vp, ctypes.POINTER(Problem), ctypes.c_double, i64,
+                                                 ctypes.POINTER(ctypes.c_uint64)]),
+        "jacobi_server_poll": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.POINTER(Result), vp]),
+        "jacobi_server_wait": (ctypes.c_int, [vp, ctypes.c_uint64, ctypes.c_double]),
+        "jacobi_server_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(ServerStats)]),
+        "jacobi_server_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -435,6 +450,93 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             jacobi_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        if not sys.is_finalizing():
+            try:
+                self.close()
+            except Exception:  # noqa: BLE001
+                pass
+
+
+def _problem_struct(p, keep):
+    """Problem struct for an inputs.Problem-like object (host numpy arrays)."""
+    ps = Problem()
+    dims, blk = list(p.dims), list(p.block)
+    ps.ndim = len(dims)
+    for a in range(3):
+        ps.dims[a] = dims[a] if a < len(dims) else 1
+        ps.block[a] = blk[a] if a < len(blk) else 1
+    bc, k = make_boundary(p.faces)
+    keep.append(k)
+    ps.bc = bc
+    for name in ("source", "x0"):
+        v = getattr(p, name)
+        if v is None:
+            setattr(ps, name, None)
+        else:
+            a_ = np.ascontiguousarray(v, dtype=np.float64)
+            keep.append(a_)
+            setattr(ps, name, a_.ctypes.data)
+    return ps
+
+
+class Server:
+    """Continuous-batching server: Server(dtype, budget_bytes, max_slots)."""
+
+    def __init__(self, dtype="f32_refine", budget_bytes=1 << 30, max_slots=64, stream=None, torch_alloc=True,
+                 **options):
+        self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
+        if torch_alloc:
+            use_torch_allocator(True)
+        self.stream = default_stream() if stream is None else stream
+        h = ctypes.c_void_p()
+        _check(load().jacobi_server_create(ctypes.byref(h), self.dtype, int(budget_bytes), int(max_slots),
+                                           self.stream), None)
+        self.h = h
+        self.shapes = {}
+        for k, v in options.items():
+            _check(load().jacobi_server_set_option(self.h, k.encode(), int(v)), None)
+
+    def submit(self, problem, tol, max_sweeps):
+        keep = []
+        ps = _problem_struct(problem, keep)
+        t = ctypes.c_uint64()
+        _check(load().jacobi_server_submit(self.h, ctypes.byref(ps), float(tol), int(max_sweeps), ctypes.byref(t)),
+               None)
+        self.shapes[t.value] = tuple(reversed(tuple(problem.dims)))
+        return t.value
+
+    def poll(self, ticket, want_field=True):
+        """None while pending, else (status, sweeps, rel, seconds, field)."""
+        r = Result()
+        out = np.empty(self.shapes[ticket], dtype=np.float64) if want_field else None
+        st = load().jacobi_server_poll(self.h, ctypes.c_uint64(ticket), ctypes.byref(r),
+                                       None if out is None else out.ctypes.data)
+        if st == ERR_BUSY:
+            return None
+        _check(st, None)
+        del self.shapes[ticket]
+        return r.status, r.sweeps, r.rel, r.seconds, out
+
+    def wait(self, ticket, timeout_s=60.0):
+        return load().jacobi_server_wait(self.h, ctypes.c_uint64(ticket), float(timeout_s)) == OK
+
+    def stats(self):
+        st = ServerStats()
+        _check(load().jacobi_server_get_stats(self.h, ctypes.byref(st)), None)
+        return {n: getattr(st, n) for n, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().jacobi_server_destroy(self.h)
             self.h = None
 
     def __enter__(self):

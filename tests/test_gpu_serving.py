@@ -1,0 +1,107 @@
+"""Serving: continuous batching under an HBM budget.
+
+Requests that arrive while others run are admitted as slots and memory free
+up; every result must equal the same solve run alone (same refine_period),
+bit for bit, and the budget must bound the resident state.
+"""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2303_02543_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_2303_02543_gb300 import jacobi as J  # noqa: E402
+
+K = 20
+MAXS = 20 * 50000
+
+
+def alone(p, dtype="f32_refine"):
+    with J.Solver(p.dims, p.block, dtype=dtype, faces=p.faces, source=p.source, x0=p.x0, refine_period=K,
+                  schedule=1) as s:
+        st, sw, rel = s.solve(1e-8, MAXS)
+        return st, sw, s.field()
+
+
+def mixed_requests():
+    return [inputs.make_problem((90, 70), (32, 32), 91, boundary="uniform", source="normal"),
+            inputs.make_problem((14, 12, 10), (8, 8, 8), 92, boundary="uniform", source="normal"),
+            inputs.make_problem((160, 40), (64, 40), 93, boundary="uniform", source="normal"),
+            inputs.make_problem((9, 9, 9), (9, 9, 9), 94, boundary="uniform", source="normal"),
+            inputs.make_problem((33, 120), (33, 64), 95, boundary="uniform", source="normal"),
+            inputs.make_problem((20, 7, 16), (10, 7, 8), 96, boundary="uniform", source="normal")]
+
+
+@pytest.mark.parametrize("dtype", ["f32_refine", "bf16_refine"])
+def test_results_equal_alone_with_staggered_arrivals(dtype):
+    probs = mixed_requests()
+    with J.Server(dtype, budget_bytes=256 << 20, max_slots=8, refine_period=K) as srv:
+        tickets = [srv.submit(p, 1e-8, MAXS) for p in probs[:3]]
+        time.sleep(0.02)                      # the first ones are running when the rest arrive
+        tickets += [srv.submit(p, 1e-8, MAXS) for p in probs[3:]]
+        outs = []
+        for t in tickets:
+            assert srv.wait(t, 120.0)
+            outs.append(srv.poll(t))
+        stats = srv.stats()
+    assert stats["completed"] == len(probs) and stats["admitted"] == len(probs)
+    for p, (st, sw, rel, secs, field) in zip(probs, outs):
+        st1, sw1, x1 = alone(p, dtype)
+        assert st == J.OK and st1 == J.OK
+        assert sw == sw1
+        assert np.array_equal(field, x1)
+        assert oracle.relative_residual(p.dims, p.faces, p.source, field) <= 1e-8 * (1 + 1e-9)
+
+
+def test_budget_bounds_resident_state_and_queues():
+    probs = [inputs.make_problem((128, 128), (64, 64), 100 + i, boundary="uniform", source="normal") for i in range(5)]
+    one = 128 * 128 * 60  # rough bytes of one solve's state
+    with J.Server("f32_refine", budget_bytes=int(2.6 * one) + (2 << 20), max_slots=8, refine_period=K) as srv:
+        tickets = [srv.submit(p, 1e-8, MAXS) for p in probs]
+        peak = 0
+        while True:
+            s = srv.stats()
+            peak = max(peak, s["active"])
+            assert s["bytes_in_use"] <= s["budget_bytes"]
+            if s["completed"] == len(probs):
+                break
+            time.sleep(0.001)
+        results = [srv.poll(t) for t in tickets]
+    assert 1 <= peak < len(probs)
+    for p, r in zip(probs, results):
+        assert r[0] == J.OK
+        assert np.array_equal(r[4], alone(p)[2])
+
+
+def test_request_larger_than_budget_is_refused():
+    with J.Server("f32_refine", budget_bytes=4 << 20, max_slots=4) as srv:
+        with pytest.raises(J.JacobiError) as e:
+            srv.submit(inputs.make_problem((1024, 1024), (128, 128), 110, source="normal"), 1e-8, MAXS)
+        assert e.value.status == J.ERR_BUSY
+        assert srv.stats()["rejected"] == 1
+
+
+def test_short_request_overtakes_long_one():
+    """Continuous batching: a small solve submitted after a big one is
+    admitted while the big one runs and finishes first."""
+    big = inputs.make_problem((400, 400), (128, 128), 120, boundary="uniform", source="normal")
+    small = inputs.make_problem((24, 24), (24, 24), 121, boundary="uniform", source="normal")
+    with J.Server("f32_refine", budget_bytes=512 << 20, max_slots=4, refine_period=K) as srv:
+        tb = srv.submit(big, 1e-8, MAXS)
+        time.sleep(0.01)
+        ts = srv.submit(small, 1e-8, MAXS)
+        assert srv.wait(ts, 60.0)
+        assert srv.poll(tb, want_field=False) is None  # the big one is still running
+        rs = srv.poll(ts)
+        assert srv.wait(tb, 300.0)
+        rb = srv.poll(tb)
+    assert rs[0] == J.OK and rb[0] == J.OK and rs[3] < rb[3]
+    assert np.array_equal(rs[4], alone(small)[2]) and np.array_equal(rb[4], alone(big)[2])
