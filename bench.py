@@ -55,7 +55,13 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poisson2d_8192",
-                    choices=["poisson2d_8192", "poisson2d_4096", "laplace2d_256", "poisson3d_512", "poisson3d_256"])
+                    choices=["poisson2d_8192", "poisson2d_4096", "laplace2d_256", "poisson3d_512", "poisson3d_256",
+                             "tts2d_512", "tts3d_128", "tts3d_512", "batched", "serving"])
+    ap.add_argument("--scale", type=float, default=0.25, help="batched: side scale (1.0 = the full 64..2048 recipe)")
+    ap.add_argument("--rate", type=float, default=10.0, help="serving: arrivals per second")
+    ap.add_argument("--window", type=float, default=20.0, help="serving: arrival window, seconds")
+    ap.add_argument("--cap2d", type=int, default=512, help="serving: largest 2D side admitted to the stream")
+    ap.add_argument("--cap3d", type=int, default=128, help="serving: largest 3D side admitted to the stream")
     ap.add_argument("--sweeps", type=int, default=0, help="override the sweeps per step (profiling runs)")
     ap.add_argument("--forms", default="f64,f32_refine,bf16_refine")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -194,6 +200,8 @@ def cpu_baseline(p, name):
 def run_reference(args, rank, world):
     if rank != 0:
         return
+    if args.workload not in ("poisson2d_8192", "poisson2d_4096", "laplace2d_256", "poisson3d_512", "poisson3d_256"):
+        args.workload = "poisson2d_8192"
     p, desc, _ = make_workload(args.workload)
     sweeps = {"poisson2d_8192": 5, "poisson2d_4096": 20, "laplace2d_256": 500, "poisson3d_512": 2,
               "poisson3d_256": 10}[args.workload]
@@ -363,11 +371,144 @@ def run_ours(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
+# ---- time to tolerance, batches, serving (separate lines, not the default) ---
+
+def run_tts(args, rank, world, local):
+    """Time to relative residual 1e-8: plain FP64 against FP32- and
+    BF16-inner refinement on the same grid and GPU (each a real solve)."""
+    import torch
+
+    import oracle
+    from paper_2303_02543_gb300 import inputs
+    from paper_2303_02543_gb300 import jacobi as J
+    torch.cuda.set_device(local)
+    n = {"tts2d_512": 512, "tts3d_128": 128, "tts3d_512": 512}[args.workload]
+    if args.workload == "tts2d_512":
+        p = inputs.make_problem((n, n), (128, 128), 2309, boundary="uniform", source="normal", x0="zero")
+    else:
+        p = inputs.poisson_3d(n=n, block=64 if n >= 256 else 32)
+    forms = [f for f in args.forms.split(",") if f]
+    out = {}
+    for form in forms:
+        opts = dict(check_every=CHECK_EVERY, refine_period=20 if p.ndim == 3 else 50, schedule=1, graph=1)
+        s = J.Solver(p.dims, p.block, dtype=form, faces=p.faces, source=p.source, **opts)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, sw, rel = s.solve(1e-8, 10 ** 9)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        x = s.field()
+        s.close()
+        rel_o = oracle.relative_residual(p.dims, p.faces, p.source, x, threads=0) if p.points <= 1 << 24 else None
+        out[form] = {"status": st, "sweeps": sw, "seconds": dt, "rel_gpu": rel, "rel_oracle": rel_o,
+                     "glups": p.points * sw / dt / 1e9}
+    base = out.get("f64", {}).get("seconds")
+    for f, r in out.items():
+        r["speedup_vs_f64"] = (base / r["seconds"]) if base else None
+    if rank == 0:
+        print(json.dumps({"metric": "time to relative residual 1e-8 (s)", "workload": args.workload,
+                          "grid": list(p.dims), "block": list(p.block), "higher_is_better": False,
+                          "forms": out, "data": "synthetic"}), flush=True)
+
+
+def run_batched(args, rank, world, local):
+    """The batched recipe (256 uneven 2D solves, sides log-uniform per axis,
+    128^2 blocks) at side scale args.scale, FP32-inner refinement to 1e-8 in
+    one persistent launch per step replayed from a CUDA graph, tiles from the
+    autotuner; compared with solving the same grids one after another."""
+    import torch
+
+    from paper_2303_02543_gb300 import inputs
+    from paper_2303_02543_gb300 import jacobi as J
+    torch.cuda.set_device(local)
+    probs = inputs.batched_2d(count=256, size_scale=args.scale)
+    pts = sum(p.points for p in probs)
+    opts = dict(refine_period=20, schedule=1, graph=1, autotune=1)
+    b = J.Batch(probs, dtype="f32_refine", **opts)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    st, res = b.solve(1e-8, 20 * 10 ** 7)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    launches = b.profile("all")[1]
+    b.close()
+    lups = sum(p.points * r[1] for p, r in zip(probs, res))
+    # the same grids one context at a time (no batching), same options
+    t1 = time.perf_counter()
+    for p in probs:
+        with J.Solver(p.dims, p.block, dtype="f32_refine", faces=p.faces, source=p.source,
+                      refine_period=20, schedule=1, graph=1) as s:
+            s.solve(1e-8, 20 * 10 ** 7)
+    torch.cuda.synchronize()
+    dt_seq = time.perf_counter() - t1
+    if rank == 0:
+        print(json.dumps({"metric": "batched solve to 1e-8: aggregate GLUP/s", "workload": "batched",
+                          "value": lups / dt / 1e9, "unit": "GLUP/s", "seconds": dt,
+                          "seconds_one_by_one": dt_seq, "speedup_vs_one_by_one": dt_seq / dt,
+                          "solves": len(probs), "points": pts, "all_ok": st == J.OK,
+                          "max_sweeps": max(r[1] for r in res), "launches": launches,
+                          "config": {"scale": args.scale, "sides": [64 * args.scale, 2048 * args.scale],
+                                     "block": 128, "refine_period": 20, "schedule": "persistent+graph",
+                                     "autotune": True}, "data": "synthetic"}), flush=True)
+
+
+def run_serving(args, rank, world, local):
+    """Poisson arrivals over a bounded window into the continuous-batching
+    server; 2D and 3D solves (sizes capped, labelled), each to 1e-8."""
+    import torch
+
+    from paper_2303_02543_gb300 import inputs
+    from paper_2303_02543_gb300 import jacobi as J
+    torch.cuda.set_device(local)
+    stream = inputs.serving_stream(rate=args.rate, window_s=args.window, lo2=128, hi2=args.cap2d, lo3=32,
+                                   hi3=args.cap3d)
+    srv = J.Server("f32_refine", budget_bytes=64 << 30, max_slots=256, refine_period=20)
+    t0 = time.perf_counter()
+    tickets = []
+    for a in stream:
+        now = time.perf_counter() - t0
+        if a.t > now:
+            time.sleep(a.t - now)
+        tickets.append((srv.submit(a.problem, 1e-8, 20 * 10 ** 7), a.problem))
+    deadline = t0 + args.window + 60.0
+    lat, lups, censored = [], 0.0, 0
+    for t, p in tickets:
+        left = deadline - time.perf_counter()
+        if left <= 0 or not srv.wait(t, left):
+            censored += 1
+            continue
+        st, sw, rel, secs, _ = srv.poll(t, want_field=False)
+        lat.append(secs)
+        lups += p.points * sw
+    wall = time.perf_counter() - t0
+    stats = srv.stats()
+    srv.close()
+    lat.sort()
+
+    def pct(q):
+        return lat[min(len(lat) - 1, int(q * len(lat)))] * 1e3 if lat else None
+    if rank == 0:
+        print(json.dumps({"metric": "serving: p50/p99 solve latency (ms) and aggregate GLUP/s", "workload": "serving",
+                          "offered_rate": args.rate, "window_s": args.window, "requests": len(tickets),
+                          "completed": len(lat), "censored": censored, "completed_per_s": len(lat) / wall,
+                          "p50_ms": pct(0.5), "p99_ms": pct(0.99), "glups": lups / wall / 1e9,
+                          "steps": stats["steps"], "higher_is_better": False,
+                          "config": {"cap2d": args.cap2d, "cap3d": args.cap3d, "dtype": "f32_refine",
+                                     "refine_period": 20, "note": "sizes capped (full 4096^2 solves take ~1 h each)"},
+                          "data": "synthetic"}), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_setup(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload.startswith("tts"):
+        run_tts(args, rank, world, local)
+    elif args.workload == "batched":
+        run_batched(args, rank, world, local)
+    elif args.workload == "serving":
+        run_serving(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

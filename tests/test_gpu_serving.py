@@ -62,9 +62,10 @@ def test_results_equal_alone_with_staggered_arrivals(dtype):
 
 
 def test_budget_bounds_resident_state_and_queues():
-    probs = [inputs.make_problem((128, 128), (64, 64), 100 + i, boundary="uniform", source="normal") for i in range(5)]
-    one = 128 * 128 * 60  # rough bytes of one solve's state
-    with J.Server("f32_refine", budget_bytes=int(2.6 * one) + (2 << 20), max_slots=8, refine_period=K) as srv:
+    # about 2.8 MB of state each (x twice, f, e twice, r, faces, partials,
+    # tables): an 8.5 MB arena holds two at a time, never three
+    probs = [inputs.make_problem((256, 256), (64, 64), 100 + i, boundary="uniform", source="normal") for i in range(5)]
+    with J.Server("f32_refine", budget_bytes=int(8.5 * (1 << 20)), max_slots=8, refine_period=K) as srv:
         tickets = [srv.submit(p, 1e-8, MAXS) for p in probs]
         peak = 0
         while True:
