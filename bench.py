@@ -64,6 +64,7 @@ def parse():
     ap.add_argument("--cap3d", type=int, default=128, help="serving: largest 3D side admitted to the stream")
     ap.add_argument("--sweeps", type=int, default=0, help="override the sweeps per step (profiling runs)")
     ap.add_argument("--forms", default="f64,f32_refine,bf16_refine")
+    ap.add_argument("--emu", type=int, default=-1, help="FP64 additions per warp step on the integer pipe (0, 2, 3)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -230,8 +231,11 @@ def run_reference(args, rank, world):
 def time_form(p, form, sweeps, args, world, stream, sampler=None):
     import torch
     from paper_2303_02543_gb300 import jacobi as J
+    opts = {}
+    if form == "f64" and args.emu >= 0:
+        opts["emu_adds"] = args.emu
     s = J.Solver(p.dims, p.block, dtype=form, faces=p.faces, source=p.source, x0=p.x0,
-                 check_every=CHECK_EVERY, refine_period=CHECK_EVERY, profile=1)
+                 check_every=CHECK_EVERY, refine_period=CHECK_EVERY, profile=1, **opts)
 
     def step():
         st, sw, rel = s.solve(1e-300, sweeps)

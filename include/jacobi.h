@@ -295,9 +295,9 @@ void jacobi_server_destroy(jacobi_server_t srv);
  *
  * Scratch: one fixed array in device global memory (a file-scope __device__
  * variable of about 8 MiB that every GPU which loads the library keeps until
- * the process exits).  The grid must satisfy ny * nz * ceil(nx / 64) <= 2^20
- * (8192 x 8192 fits; 512^3 does not); larger grids return JACOBI_ERR_INVALID
- * before any GPU work.  The first call on a device looks up the array's
+ * the process exits).  The grid must satisfy ceil(nx / 64) * ceil(ny / 8)
+ * <= 2^20 in 2D and ceil(nx / 64) * ny * ceil(nz / 8) <= 2^20 in 3D (16384^2
+ * and 512^3 fit); larger grids return JACOBI_ERR_INVALID before any GPU work.  The first call on a device looks up the array's
  * device address with that device current; make that first call before any
  * stream capture.  Every call shares the array, so calls that overlap on the
  * GPU (on different streams, or from different threads) race: order them.

@@ -228,6 +228,7 @@ static int64_t* option_slot(Options& o, const char* key) {
   if (!strcmp(key, "spin_limit")) return &o.spin_limit;
   if (!strcmp(key, "poison_wait")) return &o.poison_wait;
   if (!strcmp(key, "autotune")) return &o.autotune;
+  if (!strcmp(key, "emu_adds")) return &o.emu_adds;
   return nullptr;
 }
 
@@ -243,6 +244,7 @@ jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value) {
   if (k == "halo" || k == "profile" || k == "schedule" || k == "graph" || k == "poison_wait" || k == "autotune")
     require(value == 0 || value == 1, k + " must be 0 or 1");
   if (k == "spin_limit") require(value >= 0 && value <= 0x7fffffff, "spin_limit must be in [0, 2^31)");
+  if (k == "emu_adds") require(value == 0 || value == 2 || value == 3, "emu_adds must be 0, 2 or 3");
   const bool retable = (k == "rows_f64" || k == "rows_low") && *p != value;
   *p = value;
   if (retable) ws.rebuild_tables();

@@ -99,7 +99,15 @@ static void layout(SolveHost& s) {
     seg_base[i + 1] = seg_base[i] + (bx + kResSeg - 1) / kResSeg;
   }
   s.part_row = (int)seg_base[s.nb[0]];
-  s.nparts = (int64_t)s.part_row * p.n[1] * p.n[2];
+  // groups of kResGroup lines along the march axis (y in 2D, z in 3D),
+  // counted block by block so that no group straddles two blocks
+  const int ma = nd == 3 ? 2 : 1;
+  std::vector<int64_t> grp_base(s.nb[ma] + 1, 0);
+  for (int t = 0; t < s.nb[ma]; ++t) {
+    const int64_t ext = t < s.nb[ma] - 1 ? p.blk[ma] : p.n[ma] - (int64_t)(s.nb[ma] - 1) * p.blk[ma];
+    grp_base[t + 1] = grp_base[t] + (ext + kResGroup - 1) / kResGroup;
+  }
+  s.nparts = (int64_t)s.part_row * grp_base[s.nb[ma]] * (nd == 3 ? p.n[1] : 1);
   s.nchunks = (int)((s.nparts + kRedChunk - 1) / kRedChunk);
   s.blocks.clear();
   auto idx = [&](int i, int j, int k) { return (k * s.nb[1] + j) * s.nb[0] + i; };
@@ -138,6 +146,7 @@ static void layout(SolveHost& s) {
         for (int q = 0; q < 6; ++q) fs += B.fsz[q];
         fcursor = B.foff + fs;
         B.part = seg_base[i];
+        B.pg = (int32_t)grp_base[nd == 3 ? k : j];
         s.blocks.push_back(B);
       }
   s.elems = round_up(cursor, 32);
@@ -304,7 +313,9 @@ void Workset::rebuild_tables() {
   face_cnt_.assign(capacity_, 0);
   row_base_.assign(capacity_, 0);
   row_cnt_.assign(capacity_, 0);
-  const int r64 = (int)std::min<int64_t>(std::max<int64_t>(opt.rows_f64, 1), 32767);
+  // FP64 items hold whole residual groups (a group is reduced by one warp)
+  const int r64 = (int)std::min<int64_t>((std::max<int64_t>(opt.rows_f64, 1) + kResGroup - 1) / kResGroup * kResGroup,
+                                         32760);
   const int rlo = (int)std::min<int64_t>(std::max<int64_t>(opt.rows_low, 1), 32767);
   for (int slot = 0; slot < capacity_; ++slot) {
     SolveHost* s = solves_[slot];
@@ -604,7 +615,7 @@ void Workset::sweeps_f64(int64_t n, bool resid_last) {
     const bool resid = resid_last && k == n - 1;
     const int kpar = (int)(k & 1);
     prof_begin(kProfSweepF64);
-    LAUNCH(launch_sweep_f64(t, kpar, push, resid, true, cur_), "sweep f64");
+    LAUNCH(launch_sweep_f64(t, kpar, push, resid, true, (int)opt.emu_adds, cur_), "sweep f64");
     prof_end(kProfSweepF64);
     if (!push) {
       prof_begin(kProfHalo);
@@ -627,7 +638,7 @@ void Workset::phase_advance(int d, int set_apply_e) {
 
 void Workset::residual_only() {
   if (tables_dirty_) rebuild_tables();
-  LAUNCH(launch_sweep_f64(tables(), 0, false, true, false, cur_), "residual");
+  LAUNCH(launch_sweep_f64(tables(), 0, false, true, false, 0, cur_), "residual");
   reduce();
 }
 

@@ -40,6 +40,14 @@ JGB_HD double f64_from_bits(uint64_t u) {
 #endif
 }
 
+JGB_HD int clz64(uint64_t v) {
+#if defined(__CUDA_ARCH__)
+  return __clzll((long long)v);
+#else
+  return v ? __builtin_clzll(v) : 64;
+#endif
+}
+
 JGB_HD uint64_t umulhi64(uint64_t a, uint64_t b) {
 #if defined(__CUDA_ARCH__)
   return __umul64hi(a, b);
@@ -84,6 +92,107 @@ JGB_HD double sixth_bits(uint64_t b) {
   const uint64_t q = (Q + (1ull << (sh - 1))) >> sh;
   const uint64_t hi = (b & 0x8000000000000000ull) | ((uint64_t)(e - 6u + sh) << 52);
   return f64_from_bits(hi + q);
+}
+
+// a + b rounded to nearest-even, on the integer pipe.  Fast path: the larger
+// operand normal, the smaller normal or zero, the result normal; `ok` is
+// false otherwise and the caller must take the hardware addition.
+//
+// Textbook binary floating-point addition: order by magnitude, align the
+// smaller significand with its shifted-out bits jammed into the lowest bit
+// (10 guard bits), add or subtract, renormalise (one right shift after a
+// carry, a count of leading zeros after cancellation), round to nearest with
+// ties to even, repack.
+JGB_HD uint64_t add_bits(uint64_t a, uint64_t b, bool& ok) {
+  const uint64_t kMag = 0x7FFFFFFFFFFFFFFFull, kFrac = 0x000FFFFFFFFFFFFFull, kHid = 0x0010000000000000ull;
+  uint64_t ma = a & kMag, mb = b & kMag;
+  if (ma < mb) {
+    const uint64_t t = a;
+    a = b;
+    b = t;
+    const uint64_t u = ma;
+    ma = mb;
+    mb = u;
+  }
+  const uint32_t ea = (uint32_t)(ma >> 52), eb = (uint32_t)(mb >> 52);
+  if (mb == 0) {  // b = +-0: a + b = a, and +-0 + +-0 follows the sign rule
+    ok = true;
+    return ma == 0 ? (a & b) : a;
+  }
+  ok = (ea - 1u < 0x7FEu) && (eb - 1u < 0x7FEu);
+  const uint64_t A = ((a & kFrac) | kHid) << 10;  // leading bit at 62
+  const uint64_t B = ((b & kFrac) | kHid) << 10;
+  const uint32_t d = ea - eb;
+  uint64_t Bs;
+  if (d == 0) Bs = B;
+  else if (d < 64) Bs = (B >> d) | (uint64_t)((B << (64 - d)) != 0);
+  else Bs = 1;
+  int32_t e = (int32_t)ea;
+  uint64_t S;
+  if (((a ^ b) >> 63) == 0) {
+    S = A + Bs;
+    if (S >> 63) {
+      S = (S >> 1) | (S & 1);
+      e += 1;
+    }
+  } else {
+    S = A - Bs;
+    if (S == 0) return 0;  // exact cancellation: +0
+    const int lz = clz64(S) - 1;
+    S <<= lz;
+    e -= lz;
+  }
+  uint64_t M = S >> 10;
+  const uint32_t rem = (uint32_t)(S & 0x3FF);
+  M += (uint64_t)((rem > 0x200u) | ((rem == 0x200u) & (uint32_t)(M & 1)));
+  if (M >> 53) {
+    M >>= 1;
+    e += 1;
+  }
+  ok = ok && e >= 1 && e <= 0x7FE;
+  return (a & 0x8000000000000000ull) | (((uint64_t)(uint32_t)(e - 1) << 52) + M);
+}
+
+// float -> double, exact, for normal floats and zeros (ok false otherwise).
+JGB_HD uint64_t f32_to_f64_bits(uint32_t f, bool& ok) {
+  const uint32_t e = (f >> 23) & 0xFFu, m = f & 0x7FFFFFu;
+  const uint64_t sign = (uint64_t)(f >> 31) << 63;
+  if (e == 0 && m == 0) {
+    ok = true;
+    return sign;
+  }
+  ok = e - 1u < 254u;
+  return sign | ((uint64_t)(e + 896u) << 52) | ((uint64_t)m << 29);
+}
+
+// double -> float rounded to nearest-even when the result is a normal float
+// or a zero of a zero input (ok false otherwise).
+JGB_HD uint32_t f64_to_f32_bits(uint64_t d, bool& ok) {
+  const uint32_t sign = (uint32_t)(d >> 63) << 31;
+  const uint32_t e = (uint32_t)(d >> 52) & 0x7FFu;
+  const uint64_t mant = d & 0x000FFFFFFFFFFFFFull;
+  if (e == 0 && mant == 0) {
+    ok = true;
+    return sign;
+  }
+  const uint32_t m23 = (uint32_t)(mant >> 29);
+  const uint32_t rem = (uint32_t)(mant & 0x1FFFFFFFu);
+  const uint32_t up = (rem > 0x10000000u) | ((rem == 0x10000000u) & (m23 & 1u));
+  const uint32_t E = e - 896u;                      // biased float exponent
+  const uint32_t f = (E << 23) + m23 + up;          // a carry moves into the exponent
+  ok = (e - 897u < 254u) && ((f >> 23) - 1u < 254u);
+  return sign | f;
+}
+
+// 4 x, exact, for normal x with 4x normal and for zeros (ok false otherwise).
+JGB_HD uint64_t times4_bits(uint64_t b, bool& ok) {
+  const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+  if ((b & 0x7FFFFFFFFFFFFFFFull) == 0) {
+    ok = true;
+    return b;
+  }
+  ok = e - 1u < 0x7FCu;
+  return b + (2ull << 52);
 }
 
 }  // namespace jgb

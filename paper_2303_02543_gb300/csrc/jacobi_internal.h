@@ -28,7 +28,8 @@ constexpr int kWarps = 8;            // warps per CTA of the sweep kernels
 constexpr int kThreads = 32 * kWarps;
 constexpr int kSegF64 = 64;          // points per warp row, FP64 kernels (2 per lane)
 constexpr int kSegLow = 128;         // points per warp row, low-precision kernels (4 per lane)
-constexpr int kResSeg = 64;          // points per residual partial (fixed: decomposition independent)
+constexpr int kResSeg = 64;          // points per residual partial along x (fixed: decomposition independent)
+constexpr int kResGroup = 8;         // lines of the march axis summed into one residual partial
 constexpr int kRedThreads = 256;     // threads of the reduction kernel
 constexpr int kRedChunk = 4096;      // partials summed by one reduction CTA
 
@@ -51,7 +52,7 @@ struct BlockDev {
   int32_t ox;         // origin of the block in the solve grid (x)
   int32_t nt64;       // CTA tasks of this block in the FP64 task table
   int32_t ntlo;       // CTA tasks of this block in the low-precision task table
-  int32_t pad;
+  int32_t pg;         // first residual group of this block along the march axis (solve-wide)
 };
 
 struct SolveDev {
@@ -145,7 +146,7 @@ struct Tables {
   int poison;                        // test hook: every dependency wait runs out
 };
 
-int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, void* stream);
+int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, int emu, void* stream);
 int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, void* stream);
 int launch_refine_outer(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream);
 int launch_halo_pack(const Tables& t, int which, int par, int low, void* stream);

@@ -217,6 +217,35 @@ __device__ __forceinline__ float4 ldf4(const __nv_bfloat16* p) {
   return make_float4(lo.x, lo.y, hi.x, hi.y);
 }
 
+// float -> double and double -> float (nearest-even) on the integer pipe when
+// every lane of the warp is in the normal range, else the conversion
+// instruction (which runs on the FP64 pipe); bit-identical either way.
+__device__ __forceinline__ double f2d(float v) {
+  bool ok;
+  const double r = f64_from_bits(f32_to_f64_bits(__float_as_uint(v), ok));
+  if (__all_sync(FULL_MASK, ok)) return r;
+  return ok ? r : (double)v;
+}
+__device__ __forceinline__ float d2f(double v) {
+  bool ok;
+  const float r = __uint_as_float(f64_to_f32_bits(f64_bits(v), ok));
+  if (__all_sync(FULL_MASK, ok)) return r;
+  return ok ? r : __double2float_rn(v);
+}
+// (2d) x of the residual: 4x exactly on the integer pipe in 2D, a rounded
+// FP64 product 6x in 3D.
+template <int DIM>
+__device__ __forceinline__ double twod_x(double c) {
+  if constexpr (DIM == 2) {
+    bool ok;
+    const double r = f64_from_bits(times4_bits(f64_bits(c), ok));
+    if (__all_sync(FULL_MASK, ok)) return r;
+    return ok ? r : __dmul_rn(4.0, c);
+  } else {
+    return __dmul_rn(6.0, c);
+  }
+}
+
 // Loader of "the field value" at an element offset: x, or x + e in the outer
 // refinement step (the updated iterate x_new = x + e, formed on the fly).
 template <int MODE, typename TE, bool COH>
@@ -228,7 +257,7 @@ struct F64Src {
   __device__ __forceinline__ double one(int64_t o) const {
     double v = ldd<COH>(x + o);
     if constexpr (MODE == kModeOuter) {
-      if (apply) v = dadd(v, (double)ldf<COH>(e + o));
+      if (apply) v = dadd(v, f2d(ldf<COH>(e + o)));
     }
     return v;
   }
@@ -243,21 +272,19 @@ struct F64Src {
     b = v.y;
     if constexpr (MODE == kModeOuter) {
       if (apply) {
-        a = dadd(a, (double)ldf<COH>(e + o));
-        b = dadd(b, (double)ldf<COH>(e + o + 1));
+        a = dadd(a, f2d(ldf<COH>(e + o)));
+        b = dadd(b, f2d(ldf<COH>(e + o + 1)));
       }
     }
   }
 };
 
 template <typename TR>
-__device__ __forceinline__ void store_r(TR* p, double r);
+__device__ __forceinline__ void store_r(TR* p, float rf);
 template <>
-__device__ __forceinline__ void store_r<float>(float* p, double r) { *p = __double2float_rn(r); }
+__device__ __forceinline__ void store_r<float>(float* p, float rf) { *p = rf; }
 template <>
-__device__ __forceinline__ void store_r<__nv_bfloat16>(__nv_bfloat16* p, double r) {
-  *p = __float2bfloat16_rn(__double2float_rn(r));
-}
+__device__ __forceinline__ void store_r<__nv_bfloat16>(__nv_bfloat16* p, float rf) { *p = __float2bfloat16_rn(rf); }
 
 template <int DIM>
 __device__ __forceinline__ void push_targets(PushTargets& T, const BlockDev& B, const BlockDev* __restrict__ blocks,
@@ -302,7 +329,20 @@ __device__ __forceinline__ void push_targets(PushTargets& T, const BlockDev& B, 
 // Two points per lane, 64 per warp row.  Every load of line m+1 is issued
 // while line m is computed.
 
-template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, bool COH>
+// a + b for every lane, on the integer pipe when every lane of the warp is on
+// the software fast path (exact_f64.cuh), else on the FP64 pipe.
+__device__ __forceinline__ double dadd_int(double a, double b) {
+  bool ok;
+  const double r = f64_from_bits(add_bits(f64_bits(a), f64_bits(b), ok));
+  if (__all_sync(FULL_MASK, ok)) return r;
+  return ok ? r : dadd(a, b);
+}
+
+// EMU: how many of the seven FP64 additions of a warp step run on the
+// integer pipe instead (0; 2 = the two source additions; 3 = also the edge
+// pair of lane 0).  The FP64 pipe issues about 2 operations per clock per SM
+// on GB300 while the integer pipe is idle; results are bit-identical.
+template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, bool COH, int EMU = 0>
 __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __restrict__ blocks,
                                          const SolveDev* __restrict__ solves, int kpar, int epar) {
   constexpr bool WRITE = MODE != kModeResid;
@@ -384,6 +424,7 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   double pE = __shfl_down_sync(FULL_MASK, p0, 1);
   if (lane == 31 && east_inner) pE = src.one(G.line(m0 - 1) + x + 2);
   if (last0) c1 = a.eg;
+  double qacc = 0.0;  // residual: this lane's sum of r^2 over the current group
   double A0p = dadd(p1, c0);
   double A1p = dadd(pE, c1);
 
@@ -403,7 +444,12 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
     if ((lane == 31 && east_inner) || last1) e1 = a.eg;
     // (W + S) pair of point x: from the left lane, or formed here on lane 0
     double bw = __shfl_up_sync(FULL_MASK, A1p, 1);
-    if (lane == 0) bw = dadd(a.wv, p0);
+    if constexpr (EMU >= 3) {
+      const double be = dadd_int(a.wv, p0);
+      if (lane == 0) bw = be;
+    } else {
+      if (lane == 0) bw = dadd(a.wv, p0);
+    }
     const double A0 = dadd(c1, n0);  // P(m, x)   = c[x+1] + n[x]
     const double A1 = dadd(e1, n1);  // P(m, x+1) = c[x+2] + n[x+1]
     double t0 = dadd(bw, A0), t1 = dadd(A0p, A1);
@@ -411,8 +457,13 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
       t0 = dadd(t0, a.sn0);
       t1 = dadd(t1, a.sn1);
     }
-    t0 = dadd(t0, a.f0);
-    t1 = dadd(t1, a.f1);
+    if constexpr (EMU >= 2) {
+      t0 = dadd_int(t0, a.f0);
+      t1 = dadd_int(t1, a.f1);
+    } else {
+      t0 = dadd(t0, a.f0);
+      t1 = dadd(t1, a.f1);
+    }
 
     if constexpr (WRITE) {
       double o0, o1;
@@ -455,25 +506,33 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
       }
     }
     if constexpr (RESID || MODE == kModeOuter) {
-      const double twod = DIM == 2 ? 4.0 : 6.0;
-      const double r0 = __dsub_rn(t0, __dmul_rn(twod, c0));
-      const double r1 = __dsub_rn(t1, __dmul_rn(twod, c1));
+      const double r0 = __dsub_rn(t0, twod_x<DIM>(c0));
+      const double r1 = __dsub_rn(t1, twod_x<DIM>(c1));
       if constexpr (MODE == kModeOuter) {
+        const float rf0 = d2f(r0), rf1 = d2f(r1);
         if (v1) {
-          store_r<TR>(rout + lc + x, r0);
-          store_r<TR>(rout + lc + x + 1, r1);
+          store_r<TR>(rout + lc + x, rf0);
+          store_r<TR>(rout + lc + x + 1, rf1);
         } else if (v0) {
-          store_r<TR>(rout + lc + x, r0);
+          store_r<TR>(rout + lc + x, rf0);
         }
       }
       if constexpr (RESID) {
-        double q = v0 ? __dmul_rn(r0, r0) : 0.0;
-        if (v1) q = dadd(q, __dmul_rn(r1, r1));
+        // r^2 summed per lane over a group of kResGroup lines (line order,
+        // point order), then across the warp by a fixed butterfly: one
+        // partial per (group, 64-point segment), the same for any work split
+        if (v0) qacc = __fma_rn(r0, r0, qacc);
+        if (v1) qacc = __fma_rn(r1, r1, qacc);
+        if ((m + 1) % kResGroup == 0 || m + 1 == G.extent) {
+          double q = qacc;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) q = dadd(q, __shfl_xor_sync(FULL_MASK, q, o));
-        if (lane == 0) {
-          const int64_t row = DIM == 2 ? (int64_t)(B.oy + m) : (int64_t)(B.oz + m) * S->ny + (B.oy + y);
-          S->part[B.part + row * S->part_row + it.seg] = q;
+          for (int o = 16; o > 0; o >>= 1) q = dadd(q, __shfl_xor_sync(FULL_MASK, q, o));
+          if (lane == 0) {
+            const int64_t grp = (int64_t)B.pg + m / kResGroup;
+            const int64_t row = DIM == 2 ? grp : grp * S->ny + (B.oy + y);
+            S->part[B.part + row * S->part_row + it.seg] = q;
+          }
+          qacc = 0.0;
         }
       }
     }
@@ -489,7 +548,7 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   }
 }
 
-template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR>
+template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, int EMU = 0>
 __global__ void __launch_bounds__(kThreads, (DIM == 2 && MODE == kModeSweep) ? 3 : 1)
 k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
       const SolveDev* __restrict__ solves, int epar) {
@@ -497,7 +556,7 @@ k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* 
   if (w >= nitems) return;
   const WorkItem it = items[w];
   if (!solves[blocks[it.block].solve].active) return;
-  f64_item<DIM, MODE, PUSH, RESID, TE, TR, false>(it, blocks, solves, kpar, epar);
+  f64_item<DIM, MODE, PUSH, RESID, TE, TR, false, EMU>(it, blocks, solves, kpar, epar);
 }
 
 // ---------------------------------------------------------------------------
@@ -910,13 +969,17 @@ __global__ void k_phase_advance(SolveDev* solves, int n, int dphase, int set_app
 static inline int grid_of(int items, int per) { return (items + per - 1) / per; }
 
 template <int DIM>
-static int sweep_f64_dim(const Tables& t, int kpar, bool push, bool resid, bool write, cudaStream_t s) {
+static int sweep_f64_dim(const Tables& t, int kpar, bool push, bool resid, bool write, int emu, cudaStream_t s) {
   const dim3 g(grid_of(t.n64, kWarps)), b(kThreads);
   if (t.n64 == 0) return 0;
   if (!write) {
     k_f64<DIM, kModeResid, false, true, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
   } else if (push) {
     if (resid) k_f64<DIM, kModeSweep, true, true, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
+    else if (emu >= 3)
+      k_f64<DIM, kModeSweep, true, false, float, float, 3><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
+    else if (emu == 2)
+      k_f64<DIM, kModeSweep, true, false, float, float, 2><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
     else k_f64<DIM, kModeSweep, true, false, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
   } else {
     if (resid) k_f64<DIM, kModeSweep, false, true, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
@@ -925,10 +988,10 @@ static int sweep_f64_dim(const Tables& t, int kpar, bool push, bool resid, bool 
   return (int)cudaGetLastError();
 }
 
-int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, void* stream) {
+int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, int emu, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
-  return t.ndim == 2 ? sweep_f64_dim<2>(t, kpar, push, resid, write, s)
-                     : sweep_f64_dim<3>(t, kpar, push, resid, write, s);
+  return t.ndim == 2 ? sweep_f64_dim<2>(t, kpar, push, resid, write, emu, s)
+                     : sweep_f64_dim<3>(t, kpar, push, resid, write, emu, s);
 }
 
 template <int DIM, typename TE, typename TR>

@@ -5,15 +5,16 @@
 // in full by another runtime's pool, or a latency-bound loop that must never
 // stall, since cudaMalloc and cudaFree may synchronise the whole device.  This
 // entry point serves them.  It allocates nothing; its scratch memory (the
-// per-row partial sums, the first-level sums and the reduction ticket) lives
+// partial sums, the first-level sums and the reduction ticket) lives
 // in one file-scope __device__ array of fixed size that every GPU loading the
 // library holds until the process exits.
 //
 // The arithmetic is that of the library's fused residual: r = t - (2d) x with
-// t the neighbour sum plus source in the canonical order, r^2 summed per grid
-// row and 64-point segment by the same warp tree, then the same two-level
-// reduction.  Its result is bit-identical to jacobi_residual on a monolithic
-// context (and on any context whose block widths are multiples of 64).
+// t the neighbour sum plus source in the canonical order, r^2 summed per lane
+// over groups of 8 lines of the last axis and then across a 64-point segment
+// by the same warp tree, then the same two-level reduction.  Its result is
+// bit-identical to jacobi_residual on a monolithic context (and on any context
+// whose block extents are multiples of 64 along x and of 8 along the last axis).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -33,6 +34,7 @@ constexpr int kNaChunk = 4096;            // partials per reduction CTA
 constexpr int kNaMaxChunks = (int)(kNaMaxParts / kNaChunk);
 constexpr int kNaThreads = 256;
 constexpr int kNaWarps = 8;
+constexpr int kNaGroup = 8;               // lines per partial along the last axis (as the context kernels)
 constexpr int kMaxDevices = 64;
 
 struct NaScratch {
@@ -60,26 +62,31 @@ k_na_residual(const double* __restrict__ x, const double* __restrict__ f, NaFace
               int segs, NaScratch* __restrict__ S) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (int64_t)blockIdx.x * kNaWarps + (threadIdx.x >> 5);
-  const int64_t nwarps = (int64_t)ny * nz * segs;
+  // one warp per (group of kNaGroup lines along the last axis, [row y in 3D], segment)
+  const int ext = DIM == 2 ? ny : nz;
+  const int64_t ngroups = (ext + kNaGroup - 1) / kNaGroup;
+  const int64_t nwarps = ngroups * (DIM == 3 ? ny : 1) * segs;
   if (w >= nwarps) return;
-  const int64_t row = w / segs;
   const int seg = (int)(w % segs);
-  const int y = (int)(row % ny), z = (int)(row / ny);
-  const int64_t rb = row * nx;  // dense offset of (0, y, z)
+  const int64_t rest = w / segs;
+  const int grp = DIM == 2 ? (int)rest : (int)(rest / ny);
+  const int yfix = DIM == 2 ? 0 : (int)(rest % ny);
   const int xi = seg * 64 + 2 * lane;
   const bool v0 = xi < nx, v1 = xi + 1 < nx;
   auto X = [&](int64_t o) { return __ldg(x + o); };
   auto face = [&](int q, int64_t i) { return g.f[q] ? __ldg(g.f[q] + i) : 0.0; };
-  double r0 = 0.0, r1 = 0.0;
-  if (v0) {
+  double qacc = 0.0;
+  const int m0 = grp * kNaGroup, m1 = min(m0 + kNaGroup, ext);
+  for (int m = m0; m < m1; ++m) {
+    const int y = DIM == 2 ? m : yfix, z = DIM == 2 ? 0 : m;
+    const int64_t rb = ((int64_t)z * ny + y) * nx;  // dense offset of (0, y, z)
+    if (!v0) continue;
     const double c0 = X(rb + xi);
     const double c1 = v1 ? X(rb + xi + 1) : 0.0;
-    // x neighbours
     const double w0 = xi > 0 ? X(rb + xi - 1) : face(0, y + (int64_t)ny * z);
     const double e0 = v1 ? c1 : face(1, y + (int64_t)ny * z);
     const double w1 = c0;
     const double e1 = v1 ? (xi + 2 < nx ? X(rb + xi + 2) : face(1, y + (int64_t)ny * z)) : 0.0;
-    // y neighbours
     auto ynb = [&](int dy, int k) {
       const int yy = y + dy;
       if (yy >= 0 && yy < ny) return X(rb + (int64_t)dy * nx + xi + k);
@@ -104,14 +111,17 @@ k_na_residual(const double* __restrict__ x, const double* __restrict__ f, NaFace
               : 0.0;
     }
     const double twod = DIM == 2 ? 4.0 : 6.0;
-    r0 = __dsub_rn(t0, __dmul_rn(twod, c0));
-    r1 = v1 ? __dsub_rn(t1, __dmul_rn(twod, c1)) : 0.0;
+    const double r0 = __dsub_rn(t0, __dmul_rn(twod, c0));
+    qacc = __fma_rn(r0, r0, qacc);
+    if (v1) {
+      const double r1 = __dsub_rn(t1, __dmul_rn(twod, c1));
+      qacc = __fma_rn(r1, r1, qacc);
+    }
   }
-  double q = v0 ? __dmul_rn(r0, r0) : 0.0;
-  if (v1) q = na_add(q, __dmul_rn(r1, r1));
+  double q = qacc;
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) q = na_add(q, __shfl_xor_sync(0xffffffffu, q, o));
-  if (lane == 0) S->part[row * segs + seg] = q;
+  if (lane == 0) S->part[w] = q;
 }
 
 // Two-level deterministic reduction of S->part[0, nparts) into *out; the last
@@ -169,10 +179,12 @@ extern "C" jacobi_status jacobi_residual_noalloc(int ndim, const int64_t dims[3]
   if (nx < 1 || ny < 1 || nz < 1 || nx >= (1LL << 30) || ny >= (1LL << 30) || nz >= (1LL << 30))
     return na_fail(JACOBI_ERR_INVALID, "every dimension must be in [1, 2^30)");
   const int64_t segs = (nx + 63) / 64;
-  const int64_t nparts = segs * ny * nz;
+  const int64_t ext = ndim == 2 ? ny : nz;
+  const int64_t nparts = segs * ((ext + kNaGroup - 1) / kNaGroup) * (ndim == 3 ? ny : 1);
   if (nparts > kNaMaxParts)
-    return na_fail(JACOBI_ERR_INVALID, "grid too large for the fixed scratch: ny * nz * ceil(nx / 64) must be <= " +
-                                           std::to_string(kNaMaxParts));
+    return na_fail(JACOBI_ERR_INVALID,
+                   "grid too large for the fixed scratch: ceil(nx / 64) * ceil(n_last / 8) * (3D: ny) must be <= " +
+                       std::to_string(kNaMaxParts));
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return na_fail(JACOBI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));

@@ -131,11 +131,12 @@ def test_residual_matches_oracle(dims, block):
 
 
 def test_residual_decomposition_independent():
-    """Residual partials are keyed on global (row, 64-point segment), so any
-    decomposition whose block widths are multiples of 64 gives the same bits."""
+    """Residual partials are keyed on (group of 8 lines, 64-point segment), so
+    any decomposition whose block extents are multiples of 64 along x and of
+    8 along the march axis gives the same bits."""
     p = inputs.make_problem((256, 100), (256, 100), 47, boundary="uniform", source="normal", x0="uniform")
     vals = []
-    for b in [(256, 100), (64, 10), (128, 33), (64, 100)]:
+    for b in [(256, 100), (64, 8), (128, 32), (64, 96), (192, 40)]:
         with solver(p, block=b) as s:
             s.sweep(4)
             vals.append(s.residual())
@@ -294,3 +295,30 @@ def test_two_live_solvers_share_allocator_hooks():
     for s in (c, b, a):
         s.close()
     assert np.array_equal(xa, oracle.sweeps(p.dims, p.faces, p.source, p.x0, 4))
+
+
+@pytest.mark.parametrize("emu", [2, 3])
+@pytest.mark.parametrize("dims,block", [((300, 190), (64, 64)), ((130, 77), (64, 32)), ((37, 29, 23), (16, 8, 8)),
+                                        ((65, 1), (64, 1))])
+def test_integer_pipe_additions_bit_exact(emu, dims, block):
+    """FP64 additions moved to the integer pipe give the same bits."""
+    p = inputs.make_problem(dims, block, 56, boundary="uniform", source="normal", x0="uniform")
+    with solver(p, emu_adds=emu) as s:
+        s.sweep(11)
+        got = s.field()
+    assert np.array_equal(got, oracle.sweeps(p.dims, p.faces, p.source, p.x0, 11))
+    # zeros everywhere (f = 0, g = 0, x = 0) take the fast path's zero rule
+    q = inputs.make_problem(dims, block, 57, boundary="zero", source="zero", x0="zero")
+    with solver(q, emu_adds=emu) as s:
+        s.sweep(3)
+        assert not np.any(s.field())
+
+
+def test_residual_decomposition_independent_3d():
+    p = inputs.make_problem((130, 20, 40), (130, 20, 40), 58, boundary="uniform", source="normal", x0="uniform")
+    vals = []
+    for b in [(130, 20, 40), (64, 7, 8), (128, 20, 16), (64, 3, 24)]:
+        with solver(p, block=b) as s:
+            s.sweep(3)
+            vals.append(s.residual())
+    assert all(v == vals[0] for v in vals)

@@ -74,6 +74,6 @@ def test_noalloc_rejects_grids_beyond_its_scratch():
     x = torch.zeros(16, dtype=torch.float64, device="cuda")
     out = torch.zeros(1, dtype=torch.float64, device="cuda")
     with pytest.raises(J.JacobiError) as e:
-        J.jacobi_residual_noalloc(3, (512, 512, 512), x.data_ptr(), None, None, out.data_ptr())
+        J.jacobi_residual_noalloc(2, (1 << 16, 1 << 15), x.data_ptr(), None, None, out.data_ptr())
     assert e.value.status == J.ERR_INVALID
     assert "scratch" in J.jacobi_last_error(None)
