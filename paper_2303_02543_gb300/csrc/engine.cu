@@ -350,7 +350,7 @@ void Workset::rebuild_tables() {
         return nt;
       };
       B.nt64 = items(w64, t64, kSegF64, r64);
-      B.ntlo = refine() ? items(wlo, tlo, kSegLow, rlo) : 0;
+      B.ntlo = refine() ? items(wlo, tlo, low() == kLowBF16 ? kSegLow16 : kSegLow, rlo) : 0;
       blocks.push_back(B);
       for (int q = 0; q < 2 * ndim_; ++q) faces.push_back(FaceItem{bi, q});
       for (int z = 0; z < B.bz; ++z)

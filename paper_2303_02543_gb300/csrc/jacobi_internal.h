@@ -27,7 +27,8 @@ namespace jgb {
 constexpr int kWarps = 8;            // warps per CTA of the sweep kernels
 constexpr int kThreads = 32 * kWarps;
 constexpr int kSegF64 = 64;          // points per warp row, FP64 kernels (2 per lane)
-constexpr int kSegLow = 128;         // points per warp row, low-precision kernels (4 per lane)
+constexpr int kSegLow = 128;         // points per warp row, FP32 inner sweeps (4 per lane)
+constexpr int kSegLow16 = 256;       // points per warp row, bfloat16 inner sweeps (8 per lane)
 constexpr int kResSeg = 64;          // points per residual partial along x (fixed: decomposition independent)
 constexpr int kResGroup = 8;         // lines of the march axis summed into one residual partial
 constexpr int kRedThreads = 256;     // threads of the reduction kernel

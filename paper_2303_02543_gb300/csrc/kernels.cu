@@ -220,6 +220,8 @@ __device__ __forceinline__ float4 ldf4(const __nv_bfloat16* p) {
 // float -> double and double -> float (nearest-even) on the integer pipe when
 // every lane of the warp is in the normal range, else the conversion
 // instruction (which runs on the FP64 pipe); bit-identical either way.
+// Like every helper here that votes across the warp (div_2d, div_3d,
+// twod_x, dadd_int), these must be called by all 32 lanes together.
 __device__ __forceinline__ double f2d(float v) {
   bool ok;
   const double r = f64_from_bits(f32_to_f64_bits(__float_as_uint(v), ok));
@@ -254,26 +256,36 @@ struct F64Src {
   const TE* __restrict__ e;
   bool apply;
 
+  // Called from lane-divergent code (edge lanes only): no warp-collective
+  // operation may appear here, so the conversion is the plain instruction.
   __device__ __forceinline__ double one(int64_t o) const {
     double v = ldd<COH>(x + o);
     if constexpr (MODE == kModeOuter) {
-      if (apply) v = dadd(v, f2d(ldf<COH>(e + o)));
+      if (apply) v = dadd(v, (double)ldf<COH>(e + o));
     }
     return v;
   }
+  // Called by every lane of the warp (`valid` only predicates the loads), so
+  // the warp-voting integer conversion f2d is allowed.
   __device__ __forceinline__ void two(int64_t o, bool valid, double& a, double& b) const {
-    if (!valid) {
-      a = 0.0;
-      b = 0.0;
-      return;
+    a = 0.0;
+    b = 0.0;
+    float ea = 0.f, eb = 0.f;
+    if (valid) {
+      const double2 v = ldd2<COH>(x + o);
+      a = v.x;
+      b = v.y;
+      if constexpr (MODE == kModeOuter) {
+        if (apply) {
+          ea = ldf<COH>(e + o);
+          eb = ldf<COH>(e + o + 1);
+        }
+      }
     }
-    const double2 v = ldd2<COH>(x + o);
-    a = v.x;
-    b = v.y;
     if constexpr (MODE == kModeOuter) {
-      if (apply) {
-        a = dadd(a, f2d(ldf<COH>(e + o)));
-        b = dadd(b, f2d(ldf<COH>(e + o + 1)));
+      if (apply) {  // uniform: one flag per solve
+        a = dadd(a, f2d(ea));
+        b = dadd(b, f2d(eb));
       }
     }
   }
@@ -565,9 +577,72 @@ k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* 
 // TR.  Four points per lane, 128 per warp row.  FIRST: the input e is zero,
 // so only r is read (e' = (0 + r) / 2d).
 
+// Vector access of V consecutive low-precision values (V = 4 or 8): 16-byte
+// loads for bfloat16 and for float with V = 4, two for float with V = 8.
+template <bool COH, int V>
+__device__ __forceinline__ void ldv(const float* p, float (&o)[V]) {
+  const float4 a = ldf4<COH>(p);
+  o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  if constexpr (V == 8) {
+    const float4 b = ldf4<COH>(p + 4);
+    o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+  }
+}
+template <bool COH, int V>
+__device__ __forceinline__ void ldv(const __nv_bfloat16* p, float (&o)[V]) {
+  if constexpr (V == 4) {
+    const float4 a = ldf4<COH>(p);
+    o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+  } else {
+    uint4 u;
+    if constexpr (COH) u = __ldcg(reinterpret_cast<const uint4*>(p));
+    else u = __ldg(reinterpret_cast<const uint4*>(p));
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      o[2 * k] = __uint_as_float(w[k] << 16);
+      o[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+    }
+  }
+}
+template <int V>
+__device__ __forceinline__ void stv(float* p, const float (&v)[V], int nvalid) {
+  if (nvalid >= V) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+    if constexpr (V == 8) *reinterpret_cast<float4*>(p + 4) = make_float4(v[4], v[5], v[6], v[7]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      if (k < nvalid) p[k] = v[k];
+  }
+}
+template <int V>
+__device__ __forceinline__ void stv(__nv_bfloat16* p, const float (&v)[V], int nvalid) {
+  if (nvalid >= V) {
+    uint32_t w[V / 2];
+#pragma unroll
+    for (int k = 0; k < V / 2; ++k) {
+      const __nv_bfloat162 h = __floats2bfloat162_rn(v[2 * k], v[2 * k + 1]);
+      memcpy(&w[k], &h, 4);
+    }
+    if constexpr (V == 8) *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    else *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < V; ++k)
+      if (k < nvalid) p[k] = __float2bfloat16_rn(v[k]);
+  }
+}
+
+template <typename TE>
+__host__ __device__ constexpr int low_vpl() {
+  return sizeof(TE) == 2 ? 8 : 4;
+}
+
 template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR, bool COH>
 __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __restrict__ blocks,
                                          const SolveDev* __restrict__ solves, int epar) {
+  constexpr int V = low_vpl<TE>();
   const int lane = threadIdx.x & 31;
   const BlockDev B = blocks[it.block];
   const SolveDev* S = solves + B.solve;
@@ -578,8 +653,8 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
   const int y = it.y0;
   const Geo<DIM> G(B, y);
   const int bx = B.bx;
-  const int xs = it.seg * kSegLow;
-  const int x = xs + 4 * lane;
+  const int xs = it.seg * (32 * V);
+  const int x = xs + V * lane;
   const int nvalid = bx - x;  // > 0 when the lane holds points
   const bool any = nvalid > 0;
   const int64_t gW = B.xoff;
@@ -587,71 +662,84 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
   PushTargets T;
   if constexpr (PUSH) push_targets<DIM>(T, B, blocks, y);
 
-  const float4 zero4 = make_float4(0.f, 0.f, 0.f, 0.f);
   const int m0 = DIM == 2 ? it.y0 : it.z0;
   const int mend = m0 + it.n;
-  float4 p = zero4, c = zero4;
+  float p[V], c[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) p[k] = c[k] = 0.f;
   if constexpr (!FIRST) {
     if (any) {
-      p = ldf4<COH>(es + G.line(m0 - 1) + x);
-      c = ldf4<COH>(es + G.line(m0) + x);
+      ldv<COH, V>(es + G.line(m0 - 1) + x, p);
+      ldv<COH, V>(es + G.line(m0) + x, c);
     }
   }
   for (int m = m0; m < mend; ++m) {
     const int64_t lc = G.line(m);
     const int col = G.col(m);
-    float4 n = zero4, rv = zero4;
-    if (any) rv = ldf4<false>(rr + lc + x);  // r is read-only during every sweep
-    float4 o;
+    float rv[V], o[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) rv[k] = 0.f;
+    if (any) ldv<false, V>(rr + lc + x, rv);  // r is read-only during every sweep
+    float n[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) n[k] = 0.f;
     if constexpr (FIRST) {
-      o.x = jdivf<DIM>(__fadd_rn(0.0f, rv.x));
-      o.y = jdivf<DIM>(__fadd_rn(0.0f, rv.y));
-      o.z = jdivf<DIM>(__fadd_rn(0.0f, rv.z));
-      o.w = jdivf<DIM>(__fadd_rn(0.0f, rv.w));
+#pragma unroll
+      for (int k = 0; k < V; ++k) o[k] = jdivf<DIM>(__fadd_rn(0.0f, rv[k]));
     } else {
-      if (any) n = ldf4<COH>(es + G.line(m + 1) + x);
-      float4 sa = zero4, sb = zero4;
+      if (any) ldv<COH, V>(es + G.line(m + 1) + x, n);
+      float sa[V], sb[V];
+#pragma unroll
+      for (int k = 0; k < V; ++k) sa[k] = sb[k] = 0.f;
       if constexpr (DIM == 3) {
         if (any) {
-          sa = ldf4<COH>(es + lc - G.side + x);
-          sb = ldf4<COH>(es + lc + G.side + x);
+          ldv<COH, V>(es + lc - G.side + x, sa);
+          ldv<COH, V>(es + lc + G.side + x, sb);
         }
       }
-      // west of point 0, east of point 3
-      float wv = __shfl_up_sync(FULL_MASK, c.w, 1);
+      // west of point 0, east of point V-1
+      float wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
       if (lane == 0) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
-      float ev = __shfl_down_sync(FULL_MASK, c.x, 1);
-      if (lane == 31 && x + 4 < bx) ev = ldf<COH>(es + lc + x + 4);
+      float ev = __shfl_down_sync(FULL_MASK, c[0], 1);
+      if (lane == 31 && x + V < bx) ev = ldf<COH>(es + lc + x + V);
       float ge = 0.f;
-      if (any && nvalid <= 4) ge = ldf<COH>(es + gE + col);
-      const float cc[6] = {wv, c.x, c.y, c.z, c.w, ev};
-      float ov[4];
+      if (any && nvalid <= V) ge = ldf<COH>(es + gE + col);
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const float east = (k + 1 == nvalid) ? ge : cc[k + 2];  // the block's last point takes the ghost
-        float t = __fadd_rn(__fadd_rn(cc[k], comp(p, k)), __fadd_rn(east, comp(n, k)));
-        if constexpr (DIM == 3) t = __fadd_rn(t, __fadd_rn(comp(sa, k), comp(sb, k)));
-        t = __fadd_rn(t, comp(rv, k));
-        ov[k] = jdivf<DIM>(t);
+      for (int k = 0; k < V; ++k) {
+        const float west = k == 0 ? wv : c[k - 1];
+        float east = k == V - 1 ? ev : c[k + 1];
+        if (k + 1 == nvalid) east = ge;  // the block's last point takes the ghost
+        float t = __fadd_rn(__fadd_rn(west, p[k]), __fadd_rn(east, n[k]));
+        if constexpr (DIM == 3) t = __fadd_rn(t, __fadd_rn(sa[k], sb[k]));
+        t = __fadd_rn(t, rv[k]);
+        o[k] = jdivf<DIM>(t);
       }
-      o = make_float4(ov[0], ov[1], ov[2], ov[3]);
     }
     if (any) {
-      st4_valid<TE>(ed + lc + x, o, nvalid);
+      stv<V>(ed + lc + x, o, nvalid);
       if constexpr (PUSH) {
-        if (m == 0 && T.lo_line >= 0) st4_valid<TE>(ed + T.lo_line + x, o, nvalid);
-        if (m == G.extent - 1 && T.hi_line >= 0) st4_valid<TE>(ed + T.hi_line + x, o, nvalid);
+        if (m == 0 && T.lo_line >= 0) stv<V>(ed + T.lo_line + x, o, nvalid);
+        if (m == G.extent - 1 && T.hi_line >= 0) stv<V>(ed + T.hi_line + x, o, nvalid);
         if constexpr (DIM == 3) {
-          if (T.lo_side >= 0) st4_valid<TE>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
-          if (T.hi_side >= 0) st4_valid<TE>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
+          if (T.lo_side >= 0) stv<V>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
+          if (T.hi_side >= 0) stv<V>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
         }
-        if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o.x);
-        if (nvalid <= 4 && T.e_col >= 0) ed[T.e_col + col] = from_f<TE>(comp(o, nvalid - 1));
+        if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o[0]);
+        if (nvalid <= V && T.e_col >= 0) {
+          float last = o[0];
+#pragma unroll
+          for (int k = 1; k < V; ++k)
+            if (k == nvalid - 1) last = o[k];
+          ed[T.e_col + col] = from_f<TE>(last);
+        }
       }
     }
     if constexpr (!FIRST) {
-      p = c;
-      c = n;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        p[k] = c[k];
+        c[k] = n[k];
+      }
     }
   }
 }
