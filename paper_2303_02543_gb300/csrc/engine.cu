@@ -926,7 +926,10 @@ void Workset::autotune() {
   cuda_check(cudaEventCreate(&b), "event");
   double best = 1e300;
   int64_t best_rows = opt_rows, best_sched = opt.schedule;
-  const int64_t cand_rows[] = {8, 16, 32, 64, 128};
+  // FP64 items hold whole residual groups of 8 lines; the low-precision
+  // items may be shorter (small grids need many short items to fill the GPU)
+  std::vector<int64_t> cand_rows = {8, 16, 32, 64, 128};
+  if (ref) cand_rows.insert(cand_rows.begin(), {1, 2, 4});
   const int sweeps = 8;
   for (int64_t sc = 0; sc <= 1; ++sc) {
     for (int64_t r : cand_rows) {
