@@ -670,10 +670,12 @@ void Workset::refine_inner(int64_t k) {
     LAUNCH(launch_persist_low(t, (int)k, low(), r_bf16_, cur_), "persistent sweep low");
     prof_end(kProfSweepLow);
   } else {
+    const bool tma = opt.tma && ndim_ == 2;
     for (int64_t j = 0; j < k; ++j) {
       const int epar = (int)(j & 1);
       prof_begin(kProfSweepLow);
-      LAUNCH(launch_sweep_low(t, epar, j == 0, push, low(), r_bf16_, cur_), "sweep low");
+      if (tma && j > 0) LAUNCH(launch_sweep_low_tma(t, epar, push, low(), r_bf16_, cur_), "sweep low (staged)");
+      else LAUNCH(launch_sweep_low(t, epar, j == 0, push, low(), r_bf16_, cur_), "sweep low");
       prof_end(kProfSweepLow);
       if (!push) {
         prof_begin(kProfHalo);

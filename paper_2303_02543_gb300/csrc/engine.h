@@ -112,6 +112,7 @@ struct Options {
   int64_t poison_wait = 0;   // test hook: every dependency wait of the persistent kernel runs out
   int64_t autotune = 0;      // 1: pick rows/schedule by timing before the first solve
   int64_t emu_adds = 0;      // FP64 sweep: additions per warp step done on the integer pipe (0, 2, 3)
+  int64_t tma = 0;           // 2D inner sweeps: stage lines in shared memory with bulk async copies
 };
 
 // Outcome of one solve inside solve_all.

@@ -149,6 +149,9 @@ struct Tables {
 
 int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, int emu, void* stream);
 int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, void* stream);
+// 2D inner sweep (not the first of a step) with rows staged in shared memory
+// by bulk asynchronous copies; a timed-out wait sets ctl->status bit 1.
+int launch_sweep_low_tma(const Tables& t, int epar, bool push, int low, bool r_bf16, void* stream);
 int launch_refine_outer(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream);
 int launch_halo_pack(const Tables& t, int which, int par, int low, void* stream);
 int launch_halo_unpack(const Tables& t, int which, int par, int low, void* stream);

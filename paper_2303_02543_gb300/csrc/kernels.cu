@@ -756,6 +756,232 @@ k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict
 }
 
 // ---------------------------------------------------------------------------
+// Inner sweep with shared-memory staging by bulk asynchronous copies (2D).
+//
+// The same arithmetic as low_item, but the lines of e and r a warp needs are
+// brought into shared memory by 1D bulk copies (cp.async.bulk, completion on
+// an mbarrier) up to kTmaStages - 2 lines ahead of the line being computed,
+// so the bytes in flight do not cost registers.  Lane 0 of each warp owns its
+// warp's ring; every wait is bounded and a wait that runs out sets bit 1 of
+// *status (JACOBI_ERR_TIMEOUT on the host).
+
+constexpr int kTmaStages = 6;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(done)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+template <typename TE, typename TR>
+__host__ __device__ constexpr int tma_warp_bytes() {
+  return kTmaStages * 32 * low_vpl<TE>() * (int)(sizeof(TE) + sizeof(TR)) + kTmaStages * 8;
+}
+
+template <bool PUSH, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads)
+k_low_tma(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
+          const SolveDev* __restrict__ solves, int epar, uint32_t* status, uint32_t spin_limit) {
+  constexpr int V = low_vpl<TE>();
+  constexpr int SEGW = 32 * V;
+  constexpr int EB = SEGW * (int)sizeof(TE), RB = SEGW * (int)sizeof(TR);
+  constexpr int NS = kTmaStages;
+  extern __shared__ __align__(128) unsigned char tma_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarps + warp;
+  if (w >= nitems) return;  // whole warp; warps never synchronise with each other here
+  const WorkItem it = items[w];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  if (!S->active) return;
+  unsigned char* wb = tma_smem + warp * tma_warp_bytes<TE, TR>();
+  TE* se = reinterpret_cast<TE*>(wb);                     // NS lines of e
+  TR* sr = reinterpret_cast<TR*>(wb + NS * EB);           // NS lines of r
+  uint64_t* bars = reinterpret_cast<uint64_t*>(wb + NS * (EB + RB));
+  const TE* __restrict__ es = reinterpret_cast<const TE*>(S->e[epar ^ 1]);
+  TE* __restrict__ ed = reinterpret_cast<TE*>(S->e[epar]);
+  const TR* __restrict__ rr = reinterpret_cast<const TR*>(S->r);
+
+  const Geo<2> G(B, it.y0);
+  const int bx = B.bx;
+  const int xs = it.seg * SEGW;
+  const int x = xs + V * lane;
+  const int nvalid = bx - x;
+  const bool any = nvalid > 0;
+  const int64_t gW = B.xoff;
+  const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
+  // elements of this segment's lines that exist in the array (a multiple of
+  // 16 elements, so every copy is a multiple of 16 bytes)
+  const int cnt = min(SEGW, B.pitch - xs);
+  PushTargets T;
+  if constexpr (PUSH) push_targets<2>(T, B, blocks, it.y0);
+  const int m0 = it.y0, mend = m0 + it.n;
+  const int L0 = m0 - 1, L1 = mend;  // lines of e needed: L0..L1; lines of r: m0..mend-1
+
+  if (lane == 0) {
+    for (int k = 0; k < NS; ++k) mbar_init(&bars[k]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncwarp();
+  auto issue = [&](int L) {  // lane 0: bring line L into stage (L - L0) % NS
+    const int st = (L - L0) % NS;
+    const bool with_r = L >= m0 && L < mend;
+    const uint32_t eb = (uint32_t)(cnt * (int)sizeof(TE)), rb = with_r ? (uint32_t)(cnt * (int)sizeof(TR)) : 0u;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    mbar_expect_tx(&bars[st], eb + rb);
+    bulk_copy_g2s(se + st * SEGW, es + G.line(L) + xs, eb, &bars[st]);
+    if (with_r) bulk_copy_g2s(sr + st * SEGW, rr + G.line(L) + xs, rb, &bars[st]);
+  };
+  if (lane == 0)
+    for (int L = L0; L <= L1 && L < L0 + NS; ++L) issue(L);
+  bool failed = false;
+  auto wait_line = [&](int L) {
+    const int st = (L - L0) % NS;
+    const uint32_t par = (uint32_t)(((L - L0) / NS) & 1);
+    uint32_t iters = 0;
+    while (!mbar_try_wait(&bars[st], par)) {
+      if (++iters > spin_limit) {
+        failed = true;
+        break;
+      }
+    }
+  };
+  auto ld_stage = [&](const TE* p, float (&o)[V]) {  // V values of one line from shared memory
+    if constexpr (sizeof(TE) == 4) {
+      const float4 a = *reinterpret_cast<const float4*>(p);
+      o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else {
+      const uint4 u = *reinterpret_cast<const uint4*>(p);
+      const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        o[2 * k] = __uint_as_float(wv[k] << 16);
+        o[2 * k + 1] = __uint_as_float(wv[k] & 0xFFFF0000u);
+      }
+    }
+  };
+  auto ld_stage_r = [&](const TR* p, float (&o)[V]) {
+    if constexpr (sizeof(TR) == 4) {
+      const float4 a = *reinterpret_cast<const float4*>(p);
+      o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+      if constexpr (V == 8) {
+        const float4 b = *reinterpret_cast<const float4*>(p + 4);
+        o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+      }
+    } else {
+      const uint4 u = *reinterpret_cast<const uint4*>(p);
+      const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        o[2 * k] = __uint_as_float(wv[k] << 16);
+        o[2 * k + 1] = __uint_as_float(wv[k] & 0xFFFF0000u);
+      }
+    }
+  };
+  // edge scalars of line m, fetched one line ahead
+  auto edges = [&](int m, float& wv, float& ev, float& ge) {
+    const int64_t lc = G.line(m);
+    const int col = G.col(m);
+    wv = ev = ge = 0.f;
+    if (lane == 0) wv = xs > 0 ? ldf<false>(es + lc + xs - 1) : ldf<false>(es + gW + col);
+    if (lane == 31 && x + V < bx) ev = ldf<false>(es + lc + x + V);
+    if (any && nvalid <= V) ge = ldf<false>(es + gE + col);
+  };
+  float p[V], c[V], n[V];
+  wait_line(L0);
+  wait_line(m0);
+  if (any) {
+    ld_stage(se + ((L0 - L0) % NS) * SEGW + V * lane, p);
+    ld_stage(se + ((m0 - L0) % NS) * SEGW + V * lane, c);
+  }
+  float wv, ev, ge;
+  edges(m0, wv, ev, ge);
+  for (int m = m0; m < mend; ++m) {
+    const int64_t lc = G.line(m);
+    const int col = G.col(m);
+    float wn = 0.f, en = 0.f, gn = 0.f;
+    if (m + 1 < mend) edges(m + 1, wn, en, gn);
+    wait_line(m + 1);
+    const int stc = (m - L0) % NS, stn = (m + 1 - L0) % NS;
+    float rv[V], o[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) n[k] = rv[k] = 0.f;
+    if (any) {
+      ld_stage(se + stn * SEGW + V * lane, n);
+      ld_stage_r(sr + stc * SEGW + V * lane, rv);
+    }
+    float wl = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
+    if (lane == 0) wl = wv;
+    float el = __shfl_down_sync(FULL_MASK, c[0], 1);
+    if (lane == 31 && x + V < bx) el = ev;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const float west = k == 0 ? wl : c[k - 1];
+      float east = k == V - 1 ? el : c[k + 1];
+      if (k + 1 == nvalid) east = ge;  // the block's last point takes the ghost
+      float t = __fadd_rn(__fadd_rn(west, p[k]), __fadd_rn(east, n[k]));
+      t = __fadd_rn(t, rv[k]);
+      o[k] = jdivf<2>(t);
+    }
+    // line m-1's stage is free once every lane has read it: refill it
+    __syncwarp();
+    if (lane == 0 && m - 1 + NS <= L1) issue(m - 1 + NS);
+    if (any) {
+      stv<V>(ed + lc + x, o, nvalid);
+      if constexpr (PUSH) {
+        if (m == 0 && T.lo_line >= 0) stv<V>(ed + T.lo_line + x, o, nvalid);
+        if (m == G.extent - 1 && T.hi_line >= 0) stv<V>(ed + T.hi_line + x, o, nvalid);
+        if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o[0]);
+        if (nvalid <= V && T.e_col >= 0) {
+          float last = o[0];
+#pragma unroll
+          for (int k = 1; k < V; ++k)
+            if (k == nvalid - 1) last = o[k];
+          ed[T.e_col + col] = from_f<TE>(last);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      p[k] = c[k];
+      c[k] = n[k];
+    }
+    wv = wn;
+    ev = en;
+    ge = gn;
+  }
+  if (__any_sync(FULL_MASK, failed)) {
+    if (lane == 0) atomicOr(status, 2u);
+    // let copies still in flight land before the warp's shared memory is released
+    for (int L = max(L0, L1 - NS + 1); L <= L1; ++L) {
+      const int st = (L - L0) % NS;
+      const uint32_t par = (uint32_t)(((L - L0) / NS) & 1);
+      uint32_t iters = 0;
+      while (!mbar_try_wait(&bars[st], par) && ++iters <= spin_limit) {
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Persistent block scheduler (section 3.1.4's push/pop scheduler and the
 // implicit dependencies of section 3.1.2, moved onto the device).  A task is
 // one CTA's worth of warp items of one block; (sweep j, task t) pairs are
@@ -1228,6 +1454,26 @@ static int persist_f64_dim(const Tables& t, int nsweeps, bool resid_last, cudaSt
 int launch_persist_f64(const Tables& t, int nsweeps, bool resid_last, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   return t.ndim == 2 ? persist_f64_dim<2>(t, nsweeps, resid_last, s) : persist_f64_dim<3>(t, nsweeps, resid_last, s);
+}
+
+template <typename TE, typename TR>
+static int low_tma_typed(const Tables& t, int epar, bool push, cudaStream_t s) {
+  const int smem = kWarps * tma_warp_bytes<TE, TR>();
+  auto k = push ? k_low_tma<true, TE, TR> : k_low_tma<false, TE, TR>;
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return (int)e;
+  k<<<grid_of(t.nlo, kWarps), kThreads, smem, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar, &t.ctl->status,
+                                                   t.spin_limit);
+  return (int)cudaGetLastError();
+}
+
+int launch_sweep_low_tma(const Tables& t, int epar, bool push, int low, bool r_bf16, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.nlo == 0) return 0;
+  if (t.ndim != 2) return (int)cudaErrorInvalidValue;
+  if (low == kLowF32) return low_tma_typed<float, float>(t, epar, push, s);
+  if (r_bf16) return low_tma_typed<__nv_bfloat16, __nv_bfloat16>(t, epar, push, s);
+  return low_tma_typed<__nv_bfloat16, float>(t, epar, push, s);
 }
 
 int launch_solve_ctl(SolveDev* solves, const int32_t* ctl, int nsolves, void* stream) {

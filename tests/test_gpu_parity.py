@@ -322,3 +322,19 @@ def test_residual_decomposition_independent_3d():
             s.sweep(3)
             vals.append(s.residual())
     assert all(v == vals[0] for v in vals)
+
+
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False),
+                                           ("bf16r16_refine", True, True)])
+@pytest.mark.parametrize("dims,block", [((60, 45), (32, 16)), ((300, 70), (130, 33)), ((513, 9), (513, 9)),
+                                        ((7, 200), (7, 64))])
+def test_staged_inner_sweeps_match_oracle(dtype, e16, r16, dims, block):
+    """Inner sweeps with lines staged in shared memory by bulk copies give the
+    same bits as the register path and the oracle's emulation."""
+    p = inputs.make_problem(dims, block, 59, boundary="uniform", source="normal", x0="zero")
+    st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, 20,
+                                             e_bf16=e16, r_bf16=r16)
+    with solver(p, dtype=dtype, refine_period=20, tma=1) as s:
+        st, sw, rel = s.solve(1e-8, 10 ** 6)
+        x = s.field()
+    assert st == J.OK and sw == sw_o and np.array_equal(x, x_o)
