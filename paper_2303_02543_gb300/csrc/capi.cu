@@ -4,10 +4,19 @@
 #include <cstring>
 #include <string>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/jacobi.h"
 #include "engine.h"
 
 using namespace jgb;
+
+// NVTX range around one entry point (visible on profiler timelines; free
+// when no profiler is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
 
 struct jacobi_ctx {
   Workset* ws = nullptr;
@@ -94,6 +103,7 @@ static void fill_spec(ProblemSpec& p, int ndim, const int64_t dims[3], const int
 jacobi_status jacobi_create(jacobi_t* out, int ndim, const int64_t dims[3], const int64_t block[3], int dtype,
                             const jacobi_boundary* bc, const double* source, const double* x0, void* cuda_stream) {
   jacobi_ctx* ctx = nullptr;
+  NvtxRange nvtx_range_("jacobi_create");
   API_BEGIN
   require(out != nullptr, "out is NULL");
   *out = nullptr;
@@ -117,6 +127,7 @@ jacobi_status jacobi_create(jacobi_t* out, int ndim, const int64_t dims[3], cons
 
 jacobi_status jacobi_sweep(jacobi_t ctx, int64_t n) {
   if (!ctx) return JACOBI_ERR_INVALID;
+  NvtxRange nvtx_range_("jacobi_sweep");
   API_BEGIN
   require(n >= 0, "n must be >= 0");
   Workset& ws = *ctx->ws;
@@ -139,6 +150,7 @@ jacobi_status jacobi_sweep(jacobi_t ctx, int64_t n) {
 
 jacobi_status jacobi_residual(jacobi_t ctx, double* rel, double* abs) {
   if (!ctx) return JACOBI_ERR_INVALID;
+  NvtxRange nvtx_range_("jacobi_residual");
   API_BEGIN
   require_single(ctx);
   Workset& ws = *ctx->ws;
@@ -154,6 +166,7 @@ jacobi_status jacobi_residual(jacobi_t ctx, double* rel, double* abs) {
 
 jacobi_status jacobi_solve(jacobi_t ctx, double tol, int64_t max_sweeps, int64_t* sweeps_done, double* final_rel) {
   if (!ctx) return JACOBI_ERR_INVALID;
+  NvtxRange nvtx_range_("jacobi_solve");
   API_BEGIN
   require(tol > 0.0, "tol must be > 0");
   require(max_sweeps >= 0, "max_sweeps must be >= 0");
@@ -169,6 +182,7 @@ jacobi_status jacobi_solve(jacobi_t ctx, double tol, int64_t max_sweeps, int64_t
 
 jacobi_status jacobi_get_field(jacobi_t ctx, double* out, int on_device) {
   if (!ctx) return JACOBI_ERR_INVALID;
+  NvtxRange nvtx_range_("jacobi_get_field");
   API_BEGIN
   require(out != nullptr, "out is NULL");
   require_single(ctx);
@@ -179,6 +193,7 @@ jacobi_status jacobi_get_field(jacobi_t ctx, double* out, int on_device) {
 
 jacobi_status jacobi_set_field(jacobi_t ctx, const double* in, int on_device) {
   if (!ctx) return JACOBI_ERR_INVALID;
+  NvtxRange nvtx_range_("jacobi_set_field");
   API_BEGIN
   require(in != nullptr, "in is NULL");
   require_single(ctx);
@@ -192,6 +207,7 @@ jacobi_status jacobi_set_field(jacobi_t ctx, const double* in, int on_device) {
 
 jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device) {
   if (!ctx) return JACOBI_ERR_INVALID;
+  NvtxRange nvtx_range_("jacobi_set_source");
   API_BEGIN
   require(in != nullptr, "in is NULL");
   require_single(ctx);
@@ -311,6 +327,7 @@ const char* jacobi_last_error(jacobi_t ctx) { return ctx ? ctx->err.c_str() : t_
 
 jacobi_status jacobi_batch_create(jacobi_t* out, int n, const jacobi_problem* probs, int dtype, void* cuda_stream) {
   jacobi_ctx* ctx = nullptr;
+  NvtxRange nvtx_range_("jacobi_batch_create");
   API_BEGIN
   require(out != nullptr, "out is NULL");
   *out = nullptr;
@@ -339,6 +356,7 @@ jacobi_status jacobi_batch_create(jacobi_t* out, int n, const jacobi_problem* pr
 
 jacobi_status jacobi_batch_solve(jacobi_t ctx, double tol, int64_t max_sweeps, jacobi_result* results) {
   if (!ctx) return JACOBI_ERR_INVALID;
+  NvtxRange nvtx_range_("jacobi_batch_solve");
   API_BEGIN
   require(tol > 0.0, "tol must be > 0");
   require(max_sweeps >= 0, "max_sweeps must be >= 0");
@@ -362,6 +380,7 @@ jacobi_status jacobi_batch_solve(jacobi_t ctx, double tol, int64_t max_sweeps, j
 
 jacobi_status jacobi_batch_get_field(jacobi_t ctx, int i, double* out, int on_device) {
   if (!ctx) return JACOBI_ERR_INVALID;
+  NvtxRange nvtx_range_("jacobi_batch_get_field");
   API_BEGIN
   require(out != nullptr, "out is NULL");
   require(ctx->ws->solve(i) != nullptr, "no such problem index");

@@ -20,6 +20,8 @@
 #include <cmath>
 #include <thread>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/jacobi.h"
 #include "engine.h"
 
@@ -183,6 +185,10 @@ struct jacobi_server {
 
 // One pass of the driver: admit, step every workset once, retire.
 bool jacobi_server::step_once() {
+  nvtxRangePushA("jacobi_server_step");
+  struct PopOnExit {
+    ~PopOnExit() { nvtxRangePop(); }
+  } pop_on_exit;
   // admission: first fit, in arrival order, within the arena
   std::vector<Request> admit;
   {

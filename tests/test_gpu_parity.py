@@ -338,3 +338,30 @@ def test_staged_inner_sweeps_match_oracle(dtype, e16, r16, dims, block):
         st, sw, rel = s.solve(1e-8, 10 ** 6)
         x = s.field()
     assert st == J.OK and sw == sw_o and np.array_equal(x, x_o)
+
+
+@pytest.mark.parametrize("dtype", ["f64", "f32_refine"])
+def test_checkpoint_and_resume(dtype):
+    """A solve interrupted at a check, saved with get_field and resumed in a
+    new context from the saved field ends on the same field as one run."""
+    p = inputs.make_problem((90, 60), (32, 32), 65, boundary="uniform", source="normal", x0="zero")
+    opt = dict(check_every=20, refine_period=20)
+    with solver(p, dtype=dtype, **opt) as s:
+        st, sw, _ = s.solve(1e-8, 10 ** 6)
+        full = s.field()
+    with solver(p, dtype=dtype, **opt) as s:
+        s.solve(1e-30, 400)
+        saved = s.field()
+    q = inputs.Problem(p.dims, p.block, p.faces, p.source, saved)
+    with solver(q, dtype=dtype, **opt) as s:
+        st2, sw2, _ = s.solve(1e-8, 10 ** 6)
+        resumed = s.field()
+    assert st == st2 == J.OK
+    assert sw2 + 400 == sw
+    if dtype == "f64":
+        assert np.array_equal(resumed, full)
+    else:
+        # the pending correction is applied at the checkpoint, so the resumed
+        # run restarts its inner sweeps from r of the saved field: the same
+        # steps, bit for bit
+        assert np.array_equal(resumed, full)
