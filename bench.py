@@ -33,6 +33,8 @@ import sys
 import tempfile
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -46,7 +48,13 @@ FP64_ADD_PEAK_G = 625.0
 # FP64 additions one update needs in the canonical order with pair sharing
 FP64_ADDS_PER_LUP = {2: 3.0, 3: 5.0}
 BYTES_PER_LUP = {"f64": 24.0, "f32_refine": 12.0, "bf16_refine": 8.0}
-
+METRIC = "Jacobi GLUP/s & % HBM roofline, mixed vs FP64 at 1e-8 resid; p99 solve ms"
+# DRAM bytes (read + write) per lattice update of the 2D FP64 sweep kernel
+# (k_f64_march), from an ncu capture of a 4096^2 launch; traffic grows with
+# the points, so a full launch is this times its points.  None until that
+# capture exists for the kernel as built (it must be retaken whenever the
+# kernel changes).
+F64_SWEEP_DRAM_BYTES_PER_LUP = None
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -67,6 +75,7 @@ def parse():
     ap.add_argument("--forms", default="f64,f32_refine,bf16_refine")
     ap.add_argument("--emu", type=int, default=-1, help="FP64 additions per warp step on the integer pipe (0, 2, 3)")
     ap.add_argument("--tma", type=int, default=-1, help="2D inner sweeps staged by bulk async copies (0/1)")
+    ap.add_argument("--march", type=int, default=-1, help="2D FP64 sweeps over march items (0/1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -216,7 +225,7 @@ def run_reference(args, rank, world):
         _, _, cores = oracle_sample(p, sweeps)
     dt = time.perf_counter() - t0
     glups = p.points * sweeps * args.steps / dt / 1e9
-    line = {"impl": "reference", "metric": "Jacobi GLUP/s (FP64 plain)", "value": glups, "unit": "GLUP/s",
+    line = {"impl": "reference", "metric": METRIC, "value": glups, "unit": "GLUP/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt * 1e3 / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -236,6 +245,8 @@ def time_form(p, form, sweeps, args, world, stream, sampler=None):
     opts = {}
     if form == "f64" and args.emu >= 0:
         opts["emu_adds"] = args.emu
+    if form == "f64" and args.march >= 0:
+        opts["march"] = args.march
     if form != "f64" and args.tma >= 0:
         opts["tma"] = args.tma
     s = J.Solver(p.dims, p.block, dtype=form, faces=p.faces, source=p.source, x0=p.x0,
@@ -278,7 +289,8 @@ def e2e_form(s, p, sweeps, args, world, stream):
     """Same step through the C ABI with host buffers: upload x from pinned host
     memory, run the step, read the field back into pinned host memory."""
     import torch
-    x_host = torch.from_numpy(p.x0.copy()).pin_memory()
+    x0 = p.x0 if p.x0 is not None else np.zeros(p.shape)
+    x_host = torch.from_numpy(x0.copy()).pin_memory()
     out = torch.empty(p.shape, dtype=torch.float64).pin_memory()
     for _ in range(max(1, args.warmup - 2)):
         s.set_field(x_host)
@@ -335,8 +347,11 @@ def run_ours(args, rank, world, local):
     lup_rate = p.points / (per_launch_ms / 1e3)
     if head == "f64":
         achieved = FP64_ADDS_PER_LUP[nd] * lup_rate / 1e9
+        traffic = (F64_SWEEP_DRAM_BYTES_PER_LUP * p.points
+                   if (nd == 2 and args.emu <= 0 and args.march != 0 and F64_SWEEP_DRAM_BYTES_PER_LUP) else None)
         roof = {"bound": "alu", "kernel": "sweep_f64", "achieved": achieved, "peak": FP64_ADD_PEAK_G,
-                "unit": "GFLOP/s", "frac": achieved / FP64_ADD_PEAK_G, "traffic": None,
+                "unit": "GFLOP/s", "frac": achieved / FP64_ADD_PEAK_G, "traffic": traffic,
+                "traffic_note": "ncu dram read+write of a 4096^2 launch scaled by points" if traffic else None,
                 "peak_kind": "derived: 1.25 TFLOP/s FP64 nominal = 625 G FP64 instructions/s (adds)",
                 "hbm": {"achieved": BYTES_PER_LUP[head] * lup_rate / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": BYTES_PER_LUP[head] * lup_rate / 1e9 / hbm_peak, "peak_kind": peak_kind,
@@ -361,7 +376,7 @@ def run_ours(args, rank, world, local):
         }
         r["solver"].close()
     line = {
-        "metric": "Jacobi GLUP/s (FP64 plain; mixed forms in `forms`)",
+        "metric": METRIC,
         "value": value, "unit": "GLUP/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": h["ms"] / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if head == "f64" else head, "data": "synthetic",

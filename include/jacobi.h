@@ -161,7 +161,17 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
  *   "autotune"       1: before the first solve, time the candidate work-item
  *                    shapes and schedules and keep the fastest (cached in the
  *                    file named by the environment variable JACOBI_TUNE_CACHE)
- *   "profile"        1: time every kernel launch with CUDA events (see jacobi_profile) */
+ *   "profile"        1: time every kernel launch with CUDA events (see jacobi_profile)
+ *   "march"          1 (default): 2D FP64 sweeps that test no residual run one warp
+ *                    over every 64-point segment of a range of lines in turn,
+ *                    handing the edge pair of each line to the next segment
+ *                    (one FP64 addition per line and segment fewer); the
+ *                    ranges are sized so that all of them run in one wave
+ *   "emu_adds"       0 (default), 2 or 3: FP64 additions per warp step of the
+ *                    FP64 sweep moved to the integer pipe (bit-identical;
+ *                    slower on GB300, kept for measurement)
+ *   "tma"            1: 2D inner sweeps after the first of a refinement step
+ *                    stage their lines in shared memory by bulk async copies */
 jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value);
 jacobi_status jacobi_get_option(jacobi_t ctx, const char* key, int64_t* value);
 

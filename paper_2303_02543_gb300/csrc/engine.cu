@@ -304,7 +304,7 @@ void Workset::rebuild_tables() {
   for (void* p : table_allocs_) pool_.release(p);
   table_allocs_.clear();
   std::vector<BlockDev> blocks;
-  std::vector<WorkItem> w64, wlo;
+  std::vector<WorkItem> w64, wlo, wm;
   std::vector<CtaTask> t64, tlo;
   std::vector<FaceItem> faces;
   std::vector<RedItem> red;
@@ -317,6 +317,27 @@ void Workset::rebuild_tables() {
   const int r64 = (int)std::min<int64_t>((std::max<int64_t>(opt.rows_f64, 1) + kResGroup - 1) / kResGroup * kResGroup,
                                          32760);
   const int rlo = (int)std::min<int64_t>(std::max<int64_t>(opt.rows_low, 1), 32767);
+  // 2D FP64 march items: as many as the march kernel keeps resident (one
+  // wave), each at least 8 and at most kMarchLines lines long, the lines of a
+  // block split evenly
+  int64_t mlines = 0;
+  if (ndim_ == 2)
+    for (auto* s : solves_)
+      if (s)
+        for (const BlockDev& B : s->blocks) mlines += B.by;
+  int mlen = 8;
+  if (mlines > 0) {
+    const int64_t target = std::max(march_f64_resident_warps(ndim_, opt.halo == 0), 1);
+    auto count = [&](int len) {
+      int64_t c = 0;
+      for (auto* s : solves_)
+        if (s)
+          for (const BlockDev& B : s->blocks) c += (B.by + len - 1) / len;
+      return c;
+    };
+    mlen = (int)std::min<int64_t>(std::max<int64_t>((mlines + target - 1) / target, 8), kMarchLines);
+    while (mlen < kMarchLines && count(mlen) > target) ++mlen;
+  }
   for (int slot = 0; slot < capacity_; ++slot) {
     SolveHost* s = solves_[slot];
     if (!s) continue;
@@ -331,7 +352,8 @@ void Workset::rebuild_tables() {
       const int bi = base + (int)b;
       const int ext = ndim_ == 2 ? B.by : B.bz;
       // warp items of this block, then its CTA tasks (groups of kWarps items)
-      auto items = [&](std::vector<WorkItem>& out, std::vector<CtaTask>& tasks, int seg_w, int R) {
+      // seg_w: points per warp row; ystep (3D): block rows per warp item
+      auto items = [&](std::vector<WorkItem>& out, std::vector<CtaTask>& tasks, int seg_w, int R, int ystep) {
         const int first = (int)out.size();
         const int segs = (B.bx + seg_w - 1) / seg_w;
         for (int m0 = 0; m0 < ext; m0 += R) {
@@ -340,7 +362,7 @@ void Workset::rebuild_tables() {
             if (ndim_ == 2) {
               out.push_back(WorkItem{bi, (int16_t)sg, (int16_t)n, m0, 0});
             } else {
-              for (int y = 0; y < B.by; ++y) out.push_back(WorkItem{bi, (int16_t)sg, (int16_t)n, y, m0});
+              for (int y = 0; y < B.by; y += ystep) out.push_back(WorkItem{bi, (int16_t)sg, (int16_t)n, y, m0});
             }
           }
         }
@@ -349,8 +371,22 @@ void Workset::rebuild_tables() {
         for (int w = first; w < last; w += kWarps, ++nt) tasks.push_back(CtaTask{bi, w, std::min(kWarps, last - w), 0});
         return nt;
       };
-      B.nt64 = items(w64, t64, kSegF64, r64);
-      B.ntlo = refine() ? items(wlo, tlo, low() == kLowBF16 ? kSegLow16 : kSegLow, rlo) : 0;
+      B.nt64 = items(w64, t64, kSegF64, r64, 1);
+      if (ndim_ == 2) {
+        const int pieces = (ext + mlen - 1) / mlen;
+        for (int q = 0; q < pieces; ++q) {
+          const int a = (int)((int64_t)ext * q / pieces), e = (int)((int64_t)ext * (q + 1) / pieces);
+          wm.push_back(WorkItem{bi, 0, (int16_t)(e - a), a, 0});
+        }
+      }
+      if (refine()) {
+        // 3D rows narrower than a warp row share a warp (see low_item)
+        const int v = low() == kLowBF16 ? kSegLow16 / 32 : kSegLow / 32;
+        const int lg = ndim_ == 3 ? low_lanes_log2(B.bx, v) : 5;
+        B.ntlo = items(wlo, tlo, v << lg, rlo, 32 >> lg);
+      } else {
+        B.ntlo = 0;
+      }
       blocks.push_back(B);
       for (int q = 0; q < 2 * ndim_; ++q) faces.push_back(FaceItem{bi, q});
       for (int z = 0; z < B.bz; ++z)
@@ -373,6 +409,7 @@ void Workset::rebuild_tables() {
   d_blocks_ = (BlockDev*)up(blocks.data(), blocks.size() * sizeof(BlockDev));
   d_w64_ = (WorkItem*)up(w64.data(), w64.size() * sizeof(WorkItem));
   d_wlo_ = (WorkItem*)up(wlo.data(), wlo.size() * sizeof(WorkItem));
+  d_wm_ = (WorkItem*)up(wm.data(), wm.size() * sizeof(WorkItem));
   d_t64_ = (CtaTask*)up(t64.data(), t64.size() * sizeof(CtaTask));
   d_tlo_ = (CtaTask*)up(tlo.data(), tlo.size() * sizeof(CtaTask));
   d_faces_ = (FaceItem*)up(faces.data(), faces.size() * sizeof(FaceItem));
@@ -384,6 +421,7 @@ void Workset::rebuild_tables() {
     table_allocs_.push_back(d_done_);
   }
   n64_ = (int)w64.size();
+  nm_ = (int)wm.size();
   nlo_ = (int)wlo.size();
   nt64_ = (int)t64.size();
   ntlo_ = (int)tlo.size();
@@ -399,6 +437,8 @@ Tables Workset::tables() const {
   Tables t;
   t.w64 = d_w64_;
   t.n64 = n64_;
+  t.wm = d_wm_;
+  t.nm = nm_;
   t.wlo = d_wlo_;
   t.nlo = nlo_;
   t.faces = d_faces_;
@@ -615,7 +655,9 @@ void Workset::sweeps_f64(int64_t n, bool resid_last) {
     const bool resid = resid_last && k == n - 1;
     const int kpar = (int)(k & 1);
     prof_begin(kProfSweepF64);
-    LAUNCH(launch_sweep_f64(t, kpar, push, resid, true, (int)opt.emu_adds, cur_), "sweep f64");
+    if (opt.march && ndim_ == 2 && !resid && opt.emu_adds == 0)
+      LAUNCH(launch_sweep_f64_march(t, kpar, push, cur_), "sweep f64");
+    else LAUNCH(launch_sweep_f64(t, kpar, push, resid, true, (int)opt.emu_adds, cur_), "sweep f64");
     prof_end(kProfSweepF64);
     if (!push) {
       prof_begin(kProfHalo);
@@ -860,7 +902,7 @@ static std::string tune_key(const Workset& w, const std::vector<SolveHost*>& sol
   return s;
 }
 
-static bool tune_cache_lookup(const std::string& key, int64_t& rows, int64_t& sched) {
+static bool tune_cache_lookup(const std::string& key, int64_t& rows, int64_t& sched, int64_t& march) {
   const char* path = std::getenv("JACOBI_TUNE_CACHE");
   if (!path) return false;
   std::ifstream in(path);
@@ -874,21 +916,23 @@ static bool tune_cache_lookup(const std::string& key, int64_t& rows, int64_t& sc
     if (pr == std::string::npos || ps == std::string::npos) continue;
     r = std::atoll(line.c_str() + pr + 8);
     s = std::atoll(line.c_str() + ps + 12);
+    const size_t pm = line.find("\"march\": ");
     if (r >= 1 && (s == 0 || s == 1)) {
       rows = r;
       sched = s;
+      if (pm != std::string::npos) march = std::atoll(line.c_str() + pm + 9) != 0;
       found = true;
     }
   }
   return found;
 }
 
-static void tune_cache_store(const std::string& key, int64_t rows, int64_t sched, double us) {
+static void tune_cache_store(const std::string& key, int64_t rows, int64_t sched, int64_t march, double us) {
   const char* path = std::getenv("JACOBI_TUNE_CACHE");
   if (!path) return;
   std::ofstream out(path, std::ios::app);
   out << "{\"key\": \"" << key << "\", \"rows\": " << rows << ", \"schedule\": " << sched
-      << ", \"us_per_sweep\": " << us << "}\n";
+      << ", \"march\": " << march << ", \"us_per_sweep\": " << us << "}\n";
 }
 
 void Workset::autotune() {
@@ -896,13 +940,15 @@ void Workset::autotune() {
   if (live() == 0) return;
   const bool ref = refine();
   const std::string key = tune_key(*this, solves_, dtype_);
-  int64_t rows = 0, sched = 0;
+  int64_t rows = 0, sched = 0, march = opt.march;
   int64_t& opt_rows = ref ? opt.rows_low : opt.rows_f64;
-  if (tune_cache_lookup(key, rows, sched)) {
+  if (tune_cache_lookup(key, rows, sched, march)) {
     opt_rows = rows;
     opt.schedule = sched;
+    opt.march = march;
     rebuild_tables();
-    tune_summary_ = "cache: rows " + std::to_string(rows) + ", schedule " + std::to_string(sched);
+    tune_summary_ = "cache: rows " + std::to_string(rows) + ", schedule " + std::to_string(sched) + ", march " +
+                    std::to_string(march);
     return;
   }
   // snapshot of every FP64 iterate so the timing sweeps leave no trace
@@ -927,16 +973,27 @@ void Workset::autotune() {
   cuda_check(cudaEventCreate(&a), "event");
   cuda_check(cudaEventCreate(&b), "event");
   double best = 1e300;
-  int64_t best_rows = opt_rows, best_sched = opt.schedule;
+  int64_t best_rows = opt_rows, best_sched = opt.schedule, best_march = opt.march;
   // FP64 items hold whole residual groups of 8 lines; the low-precision
   // items may be shorter (small grids need many short items to fill the GPU)
   std::vector<int64_t> cand_rows = {8, 16, 32, 64, 128};
   if (ref) cand_rows.insert(cand_rows.begin(), {1, 2, 4});
+  struct Cand {
+    int64_t rows, sched, march;
+  };
+  std::vector<Cand> cands;
+  for (int64_t sc = 0; sc <= 1; ++sc)
+    for (int64_t r : cand_rows) cands.push_back(Cand{r, sc, ref ? opt.march : 0});
+  // FP64 march items are sized by the workset itself; rows only shapes the
+  // residual sweeps then
+  if (!ref) cands.push_back(Cand{32, 0, 1});
   const int sweeps = 8;
-  for (int64_t sc = 0; sc <= 1; ++sc) {
-    for (int64_t r : cand_rows) {
+  {
+    for (const Cand& cd : cands) {
+      const int64_t r = cd.rows, sc = cd.sched;
       opt_rows = r;
       opt.schedule = sc;
+      opt.march = cd.march;
       rebuild_tables();
       auto run = [&]() {
         if (ref) refine_inner(sweeps);
@@ -953,6 +1010,7 @@ void Workset::autotune() {
         best = ms;
         best_rows = r;
         best_sched = sc;
+        best_march = cd.march;
       }
     }
   }
@@ -962,6 +1020,7 @@ void Workset::autotune() {
   opt.graph = graph;
   opt_rows = best_rows;
   opt.schedule = best_sched;
+  opt.march = best_march;
   rebuild_tables();
   // restore the iterates and phases the timing sweeps changed
   if (!ref) {
@@ -982,9 +1041,9 @@ void Workset::autotune() {
     if (solves_[k] && solves_[k]->phase != phases[k]) ctl[k] = (solves_[k]->active ? 1 : 0) | 2;
   apply_slot_ctl(ctl);
   const double us = best * 1e3 / sweeps;
-  tune_cache_store(key, best_rows, best_sched, us);
+  tune_cache_store(key, best_rows, best_sched, best_march, us);
   tune_summary_ = "measured: rows " + std::to_string(best_rows) + ", schedule " + std::to_string(best_sched) +
-                  ", " + std::to_string(us) + " us per sweep";
+                  ", march " + std::to_string(best_march) + ", " + std::to_string(us) + " us per sweep";
 }
 
 // ---------------------------------------------------------------------------

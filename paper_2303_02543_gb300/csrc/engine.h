@@ -113,6 +113,7 @@ struct Options {
   int64_t autotune = 0;      // 1: pick rows/schedule by timing before the first solve
   int64_t emu_adds = 0;      // FP64 sweep: additions per warp step done on the integer pipe (0, 2, 3)
   int64_t tma = 0;           // 2D inner sweeps: stage lines in shared memory with bulk async copies
+  int64_t march = 1;         // FP64 sweeps without a residual: one warp computes all segments of a line range
 };
 
 // Outcome of one solve inside solve_all.
@@ -223,6 +224,8 @@ class Workset {
   BlockDev* d_blocks_ = nullptr;
   WorkItem* d_w64_ = nullptr;
   WorkItem* d_wlo_ = nullptr;
+  WorkItem* d_wm_ = nullptr;
+  int nm_ = 0;
   CtaTask* d_t64_ = nullptr;
   CtaTask* d_tlo_ = nullptr;
   uint32_t* d_done_ = nullptr;

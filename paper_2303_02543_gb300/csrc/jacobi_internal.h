@@ -31,6 +31,15 @@ constexpr int kSegLow = 128;         // points per warp row, FP32 inner sweeps (
 constexpr int kSegLow16 = 256;       // points per warp row, bfloat16 inner sweeps (8 per lane)
 constexpr int kResSeg = 64;          // points per residual partial along x (fixed: decomposition independent)
 constexpr int kResGroup = 8;         // lines of the march axis summed into one residual partial
+// log2 of the lanes one block row takes in a 3D low-precision warp item:
+// enough for bx points at v per lane, a power of two, at most 32
+__host__ __device__ inline int low_lanes_log2(int bx, int v) {
+  const int need = (bx + v - 1) / v;
+  int lg = 0;
+  while (lg < 5 && (1 << lg) < need) ++lg;
+  return lg;
+}
+constexpr int kMarchLines = 64;      // most lines in one FP64 march item (its shared-memory pair buffer)
 constexpr int kRedThreads = 256;     // threads of the reduction kernel
 constexpr int kRedChunk = 4096;      // partials summed by one reduction CTA
 
@@ -133,6 +142,7 @@ struct RowItem {
 struct Tables {
   const WorkItem* w64;  int n64;     // FP64 sweep / residual / refine-outer items
   const WorkItem* wlo;  int nlo;     // low-precision sweep items
+  const WorkItem* wm;   int nm;      // FP64 march items (all segments of a line range)
   const FaceItem* faces; int nfaces; // interior faces
   const RedItem* red;   int nred;    // reduction CTAs
   const RowItem* rows;  int nrows;   // block rows
@@ -148,6 +158,11 @@ struct Tables {
 };
 
 int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, int emu, void* stream);
+// 2D FP64 sweep (no residual) over the march items
+int launch_sweep_f64_march(const Tables& t, int kpar, bool push, void* stream);
+// warps of the 2D march sweep resident at once on the current device (0 on
+// error or in 3D)
+int march_f64_resident_warps(int ndim, bool push);
 int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, void* stream);
 // 2D inner sweep (not the first of a step) with rows staged in shared memory
 // by bulk asynchronous copies; a timed-out wait sets ctl->status bit 1.

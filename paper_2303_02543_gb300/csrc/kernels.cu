@@ -250,44 +250,78 @@ __device__ __forceinline__ double twod_x(double c) {
 
 // Loader of "the field value" at an element offset: x, or x + e in the outer
 // refinement step (the updated iterate x_new = x + e, formed on the fly).
+// Loads are split into fetch (issue the loads into registers) and fin (the
+// additions of x + e), so a kernel can issue the loads of a later line and
+// only wait for them where it consumes the values.
 template <int MODE, typename TE, bool COH>
 struct F64Src {
   const double* __restrict__ x;
   const TE* __restrict__ e;
   bool apply;
 
+  struct Raw1 {
+    double v;
+    float e;
+  };
+  struct Raw2 {
+    double a, b;
+    float ea, eb;
+  };
+
+  __device__ __forceinline__ void fetch1(int64_t o, Raw1& r) const {
+    r.v = ldd<COH>(x + o);
+    r.e = 0.f;
+    if constexpr (MODE == kModeOuter) {
+      if (apply) r.e = ldf<COH>(e + o);
+    }
+  }
   // Called from lane-divergent code (edge lanes only): no warp-collective
   // operation may appear here, so the conversion is the plain instruction.
-  __device__ __forceinline__ double one(int64_t o) const {
-    double v = ldd<COH>(x + o);
+  __device__ __forceinline__ double fin1(const Raw1& r) const {
     if constexpr (MODE == kModeOuter) {
-      if (apply) v = dadd(v, (double)ldf<COH>(e + o));
+      if (apply) return dadd(r.v, (double)r.e);
     }
-    return v;
+    return r.v;
   }
-  // Called by every lane of the warp (`valid` only predicates the loads), so
-  // the warp-voting integer conversion f2d is allowed.
-  __device__ __forceinline__ void two(int64_t o, bool valid, double& a, double& b) const {
-    a = 0.0;
-    b = 0.0;
-    float ea = 0.f, eb = 0.f;
+  __device__ __forceinline__ double one(int64_t o) const {
+    Raw1 r;
+    fetch1(o, r);
+    return fin1(r);
+  }
+  // `valid` only predicates the loads
+  __device__ __forceinline__ void fetch2(int64_t o, bool valid, Raw2& r) const {
+    r.a = 0.0;
+    r.b = 0.0;
+    r.ea = 0.f;
+    r.eb = 0.f;
     if (valid) {
       const double2 v = ldd2<COH>(x + o);
-      a = v.x;
-      b = v.y;
+      r.a = v.x;
+      r.b = v.y;
       if constexpr (MODE == kModeOuter) {
         if (apply) {
-          ea = ldf<COH>(e + o);
-          eb = ldf<COH>(e + o + 1);
+          r.ea = ldf<COH>(e + o);
+          r.eb = ldf<COH>(e + o + 1);
         }
       }
     }
+  }
+  // Called by every lane of the warp, so the warp-voting integer conversion
+  // f2d is allowed.
+  __device__ __forceinline__ void fin2(const Raw2& r, double& a, double& b) const {
+    a = r.a;
+    b = r.b;
     if constexpr (MODE == kModeOuter) {
       if (apply) {  // uniform: one flag per solve
-        a = dadd(a, f2d(ea));
-        b = dadd(b, f2d(eb));
+        a = dadd(a, f2d(r.ea));
+        b = dadd(b, f2d(r.eb));
       }
     }
+  }
+  __device__ __forceinline__ void two(int64_t o, bool valid, double& a, double& b) const {
+    Raw2 r;
+    fetch2(o, valid, r);
+    fin2(r, a, b);
   }
 };
 
@@ -354,9 +388,18 @@ __device__ __forceinline__ double dadd_int(double a, double b) {
 // integer pipe instead (0; 2 = the two source additions; 3 = also the edge
 // pair of lane 0).  The FP64 pipe issues about 2 operations per clock per SM
 // on GB300 while the integer pipe is idle; results are bit-identical.
-template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, bool COH, int EMU = 0>
+//
+// MARCH: the item is one of several segments of a block row range that the
+// same warp computes left to right.  Lane 31 keeps its pair P(m-1, x+1) of
+// every line in `wr`; for the next segment that pair is P(m-1, xs-1), the
+// (W + S) pair lane 0 would otherwise form, so lane 0 reads it from `rd`
+// (bit for bit the same value: addition is commutative) and the warp issues
+// one FP64 addition fewer per line.
+template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, bool COH, int EMU = 0,
+          bool MARCH = false>
 __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __restrict__ blocks,
-                                         const SolveDev* __restrict__ solves, int kpar, int epar) {
+                                         const SolveDev* __restrict__ solves, int kpar, int epar,
+                                         const double* rd = nullptr, double* wr = nullptr) {
   constexpr bool WRITE = MODE != kModeResid;
   const int lane = threadIdx.x & 31;
   const BlockDev B = blocks[it.block];
@@ -392,21 +435,28 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   // is last), the source, and in 3D the side rows.
   // A lane needs at most two edge values: `wv` (lane 0) and one of `eg`
   // (lane 31 or the lane whose point 1 is last: east of point 1; the lane
-  // whose point 0 is last: its east ghost).
+  // whose point 0 is last: its east ghost).  fetch_aux only issues loads;
+  // fin_aux forms the values where the next line starts.
+  using Src = F64Src<MODE, TE, COH>;
   struct LineAux {
+    typename Src::Raw1 egr, wvr;
+    typename Src::Raw2 sr, qr;  // 3D: rows y-1 and y+1
     double eg;   // x[m][x+2], or the east ghost of point 1 or of point 0
     double wv;   // lane 0: x[m][xs-1] or the west ghost
     double f0, f1;
     double sn0, sn1;
   };
-  auto load_aux = [&](int m, LineAux& a) {
+  const bool has_eg = (lane == 31 && east_inner) || last1 || last0;
+  const bool has_wv = lane == 0 && !(MARCH && xs > 0);
+  auto fetch_aux = [&](int m, LineAux& a) {
     const int64_t lc = G.line(m);
     const int col = G.col(m);
-    a.eg = 0.0;
-    a.wv = 0.0;
-    if (lane == 31 && east_inner) a.eg = src.one(lc + x + 2);
-    if (last1 || last0) a.eg = src.one(gE + col);
-    if (lane == 0) a.wv = xs > 0 ? src.one(lc + xs - 1) : src.one(gW + col);
+    if (lane == 31 && east_inner) src.fetch1(lc + x + 2, a.egr);
+    if (last1 || last0) src.fetch1(gE + col, a.egr);
+    if (has_wv) {
+      if (xs > 0) src.fetch1(lc + xs - 1, a.wvr);
+      else src.fetch1(gW + col, a.wvr);
+    }
     a.f0 = 0.0;
     a.f1 = 0.0;
     if (v0) {
@@ -414,12 +464,22 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
       a.f0 = fv.x;
       a.f1 = fv.y;
     }
+    if constexpr (DIM == 3) {
+      src.fetch2(lc - G.side + x, v0, a.sr);
+      src.fetch2(lc + G.side + x, v0, a.qr);
+    }
+  };
+  auto fin_aux = [&](LineAux& a) {
+    a.eg = 0.0;
+    a.wv = 0.0;
+    if (has_eg) a.eg = src.fin1(a.egr);
+    if (has_wv) a.wv = src.fin1(a.wvr);
     a.sn0 = 0.0;
     a.sn1 = 0.0;
     if constexpr (DIM == 3) {
       double s0, s1, q0, q1;
-      src.two(lc - G.side + x, v0, s0, s1);
-      src.two(lc + G.side + x, v0, q0, q1);
+      src.fin2(a.sr, s0, s1);
+      src.fin2(a.qr, q0, q1);
       a.sn0 = dadd(s0, q0);
       a.sn1 = dadd(s1, q1);
     }
@@ -431,7 +491,8 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   src.two(G.line(m0) + x, v0, c0, c1);
   src.two(G.line(m0 + 1) + x, v0, n0, n1);
   LineAux a;
-  load_aux(m0, a);
+  fetch_aux(m0, a);
+  fin_aux(a);
   // prologue pairs of line m-1: A0p = P(m-1, x) = p[x+1] + c[x]; A1p = P(m-1, x+1)
   double pE = __shfl_down_sync(FULL_MASK, p0, 1);
   if (lane == 31 && east_inner) pE = src.one(G.line(m0 - 1) + x + 2);
@@ -444,19 +505,26 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
     const int64_t lc = G.line(m);
     const int col = G.col(m);
     // prefetch line m+2 and the aux values of line m+1
-    double nn0 = 0.0, nn1 = 0.0;
+    typename Src::Raw2 nnr;
     LineAux an;
     const bool more = m + 1 < mend;
     if (more) {
-      src.two(G.line(m + 2) + x, v0, nn0, nn1);
-      load_aux(m + 1, an);
+      src.fetch2(G.line(m + 2) + x, v0, nnr);
+      fetch_aux(m + 1, an);
     }
     // east neighbour of point x+1 on line m
     double e1 = __shfl_down_sync(FULL_MASK, c0, 1);
     if ((lane == 31 && east_inner) || last1) e1 = a.eg;
     // (W + S) pair of point x: from the left lane, or formed here on lane 0
     double bw = __shfl_up_sync(FULL_MASK, A1p, 1);
-    if constexpr (EMU >= 3) {
+    if constexpr (MARCH) {
+      if (lane == 31) wr[m - m0] = A1p;
+      if (xs > 0) {
+        if (lane == 0) bw = rd[m - m0];
+      } else if (lane == 0) {
+        bw = dadd(a.wv, p0);
+      }
+    } else if constexpr (EMU >= 3) {
       const double be = dadd_int(a.wv, p0);
       if (lane == 0) bw = be;
     } else {
@@ -548,6 +616,10 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
         }
       }
     }
+    if (!more) break;
+    double nn0, nn1;
+    src.fin2(nnr, nn0, nn1);
+    fin_aux(an);
     A0p = A0;
     A1p = A1;
     p0 = c0;
@@ -561,7 +633,8 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
 }
 
 template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, int EMU = 0>
-__global__ void __launch_bounds__(kThreads, (DIM == 2 && MODE == kModeSweep) ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, DIM == 2 && (MODE == kModeSweep || MODE == kModeOuter) ? 3
+                                            : (MODE == kModeOuter ? 2 : 1))
 k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
       const SolveDev* __restrict__ solves, int epar) {
   const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -569,6 +642,29 @@ k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* 
   const WorkItem it = items[w];
   if (!solves[blocks[it.block].solve].active) return;
   f64_item<DIM, MODE, PUSH, RESID, TE, TR, false, EMU>(it, blocks, solves, kpar, epar);
+}
+
+// 2D FP64 sweep over march items: one warp per (block, range of lines),
+// computing every 64-point segment of the block in turn.  The pairs
+// lane 31 leaves in shared memory for the next segment alternate between two
+// buffers, so a segment never overwrites what it is still reading.
+template <int DIM, bool PUSH>
+__global__ void __launch_bounds__(kThreads, 3)
+k_f64_march(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
+            const SolveDev* __restrict__ solves) {
+  __shared__ double pairs[kWarps][2][kMarchLines];
+  const int wi = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarps + wi;
+  if (w >= nitems) return;
+  WorkItem it = items[w];
+  if (!solves[blocks[it.block].solve].active) return;
+  const int nseg = (blocks[it.block].bx + kSegF64 - 1) / kSegF64;
+  for (int sg = 0; sg < nseg; ++sg) {
+    it.seg = (int16_t)sg;
+    f64_item<DIM, kModeSweep, PUSH, false, float, float, false, 0, true>(it, blocks, solves, kpar, 0,
+                                                                         pairs[wi][(sg + 1) & 1], pairs[wi][sg & 1]);
+    __syncwarp();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -650,17 +746,24 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
   TE* __restrict__ ed = reinterpret_cast<TE*>(S->e[epar]);
   const TR* __restrict__ rr = reinterpret_cast<const TR*>(S->r);
 
-  const int y = it.y0;
-  const Geo<DIM> G(B, y);
+  // 3D: a block row narrower than a warp row takes L = 2^lgL lanes and the
+  // warp computes 32 / L adjacent rows y0, y0+1, ... (lanes of rows past the
+  // block's last row stay idle); 2D: one row of 32 lanes
+  const int lgL = DIM == 3 ? low_lanes_log2(B.bx, V) : 5;
+  const int L = 1 << lgL;
+  const int l = lane & (L - 1);
+  const int y = DIM == 3 ? it.y0 + (lane >> lgL) : it.y0;
+  const bool row_ok = DIM == 2 || y < B.by;
+  const Geo<DIM> G(B, row_ok ? y : B.by - 1);
   const int bx = B.bx;
-  const int xs = it.seg * (32 * V);
-  const int x = xs + V * lane;
-  const int nvalid = bx - x;  // > 0 when the lane holds points
+  const int xs = it.seg * (L * V);
+  const int x = xs + V * l;
+  const int nvalid = row_ok ? bx - x : 0;  // > 0 when the lane holds points
   const bool any = nvalid > 0;
   const int64_t gW = B.xoff;
   const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
   PushTargets T;
-  if constexpr (PUSH) push_targets<DIM>(T, B, blocks, y);
+  if constexpr (PUSH) push_targets<DIM>(T, B, blocks, row_ok ? y : B.by - 1);
 
   const int m0 = DIM == 2 ? it.y0 : it.z0;
   const int mend = m0 + it.n;
@@ -697,11 +800,11 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
           ldv<COH, V>(es + lc + G.side + x, sb);
         }
       }
-      // west of point 0, east of point V-1
-      float wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
-      if (lane == 0) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
-      float ev = __shfl_down_sync(FULL_MASK, c[0], 1);
-      if (lane == 31 && x + V < bx) ev = ldf<COH>(es + lc + x + V);
+      // west of point 0, east of point V-1 (shuffles stay inside the row's L lanes)
+      float wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1, L);
+      if (l == 0 && any) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
+      float ev = __shfl_down_sync(FULL_MASK, c[0], 1, L);
+      if (l == L - 1 && any && x + V < bx) ev = ldf<COH>(es + lc + x + V);
       float ge = 0.f;
       if (any && nvalid <= V) ge = ldf<COH>(es + gE + col);
 #pragma unroll
@@ -745,7 +848,7 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
 }
 
 template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, DIM == 2 && sizeof(TE) == 2 ? 3 : 1)
 k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
       const SolveDev* __restrict__ solves, int epar) {
   const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -1000,21 +1103,27 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t* p) {
   return v;
 }
 
+// Called by the 32 lanes of one warp: lane 0 watches block b, lanes 1..6 its
+// neighbours, all at once (one L2 round trip instead of seven in a row).
 template <bool LOW>
 __device__ bool wait_deps(const BlockDev& B, int b, const BlockDev* __restrict__ blocks, const uint32_t* done, int j,
                           SchedCtl* ctl, uint32_t spin_limit, int poison) {
-  for (int k = -1; k < 6; ++k) {
-    const int q = k < 0 ? b : B.nbr[k];
-    if (q < 0) continue;
-    const int nt = k < 0 ? (LOW ? B.ntlo : B.nt64) : (LOW ? blocks[q].ntlo : blocks[q].nt64);
+  const int lane = threadIdx.x & 31;
+  const int q = lane == 0 ? b : (lane < 7 ? B.nbr[lane - 1] : -1);
+  bool ok = true;
+  if (q >= 0) {
+    const int nt = lane == 0 ? (LOW ? B.ntlo : B.nt64) : (LOW ? blocks[q].ntlo : blocks[q].nt64);
     const uint32_t need = poison ? 0xffffffffu : (uint32_t)j * (uint32_t)nt;
     uint32_t iters = 0;
     while (ld_acquire_u32(done + q) < need) {
-      if (++iters > spin_limit || *(volatile uint32_t*)&ctl->status != 0u) return false;
-      __nanosleep(128);
+      if (++iters > spin_limit || *(volatile uint32_t*)&ctl->status != 0u) {
+        ok = false;
+        break;
+      }
+      __nanosleep(64);
     }
   }
-  return true;
+  return __all_sync(FULL_MASK, ok);
 }
 
 template <bool LOW, typename Body>
@@ -1039,12 +1148,15 @@ __device__ __forceinline__ void persist_loop(const CtaTask* __restrict__ tasks, 
     const CtaTask T = tasks[idx - j * ntasks];
     const BlockDev& B = blocks[T.block];
     const bool act = solves[B.solve].active != 0;
-    if (threadIdx.x == 0 && act && j > 0) {
-      if (!wait_deps<LOW>(B, T.block, blocks, done, j, ctl, spin_limit, poison)) {
-        if (atomicExch(&ctl->status, 1u) == 0u) ctl->fail_task = (uint32_t)idx;
-        s_stop = 1;
+    if (warp == 0 && act && j > 0) {
+      const bool ok = wait_deps<LOW>(B, T.block, blocks, done, j, ctl, spin_limit, poison);
+      if (threadIdx.x == 0) {
+        if (!ok) {
+          if (atomicExch(&ctl->status, 1u) == 0u) ctl->fail_task = (uint32_t)idx;
+          s_stop = 1;
+        }
+        __threadfence();
       }
-      __threadfence();
     }
     __syncthreads();
     if (s_stop) break;
@@ -1300,6 +1412,28 @@ static int sweep_f64_dim(const Tables& t, int kpar, bool push, bool resid, bool 
     else k_f64<DIM, kModeSweep, false, false, float, float><<<g, b, 0, s>>>(t.w64, t.n64, kpar, t.blocks, t.solves, 0);
   }
   return (int)cudaGetLastError();
+}
+
+int launch_sweep_f64_march(const Tables& t, int kpar, bool push, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.nm == 0) return 0;
+  const dim3 g(grid_of(t.nm, kWarps)), b(kThreads);
+  if (t.ndim != 2) return (int)cudaErrorInvalidValue;
+  if (push) k_f64_march<2, true><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves);
+  else k_f64_march<2, false><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves);
+  return (int)cudaGetLastError();
+}
+
+int march_f64_resident_warps(int ndim, bool push) {
+  int dev = 0, sms = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  if (ndim != 2) return 0;
+  const cudaError_t e =
+      push ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march<2, true>, kThreads, 0)
+           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march<2, false>, kThreads, 0);
+  if (e != cudaSuccess) return 0;
+  return per_sm * sms * kWarps;
 }
 
 int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, int emu, void* stream) {

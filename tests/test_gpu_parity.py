@@ -196,8 +196,13 @@ def test_solve_cap_and_continue():
 
 # ---- mixed-precision refinement ---------------------------------------------
 
-@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False)])
-@pytest.mark.parametrize("dims,block", [((60, 45), (32, 16)), ((16, 14, 12), (8, 7, 6))])
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False),
+                                           ("bf16r16_refine", True, True)])
+@pytest.mark.parametrize("dims,block", [((60, 45), (32, 16)), ((16, 14, 12), (8, 7, 6)),
+                                        # 3D rows narrower than a warp row: 2-16 rows per warp,
+                                        # row counts that leave idle lanes, remainder blocks
+                                        ((40, 33, 20), (32, 11, 20)), ((70, 9, 8), (64, 5, 4)),
+                                        ((130, 6, 7), (130, 6, 7))])
 def test_refine_matches_oracle_emulation(dtype, e16, r16, dims, block):
     p = inputs.make_problem(dims, block, 50, boundary="uniform", source="normal", x0="zero")
     period = 20
@@ -312,6 +317,23 @@ def test_integer_pipe_additions_bit_exact(emu, dims, block):
     with solver(q, emu_adds=emu) as s:
         s.sweep(3)
         assert not np.any(s.field())
+
+
+@pytest.mark.parametrize("halo", [0, 1])
+@pytest.mark.parametrize("dims,block", [((300, 190), (300, 190)), ((1000, 300), (200, 150)), ((130, 77), (64, 32)),
+                                        ((257, 700), (257, 700)), ((37, 29, 23), (16, 8, 8)),
+                                        ((200, 9, 150), (130, 9, 150)), ((65, 1), (64, 1)), ((3, 2), (1, 1))])
+def test_march_items_bit_exact(halo, dims, block):
+    """One warp over all segments of a line range (edge pairs handed on in
+    shared memory) gives the bits of the per-segment items and of the oracle."""
+    p = inputs.make_problem(dims, block, 59, boundary="uniform", source="normal", x0="uniform")
+    out = {}
+    for march in (0, 1):
+        with solver(p, march=march, halo=halo) as s:
+            s.sweep(9)
+            out[march] = s.field()
+    assert np.array_equal(out[1], out[0])
+    assert np.array_equal(out[1], oracle.sweeps(p.dims, p.faces, p.source, p.x0, 9))
 
 
 def test_residual_decomposition_independent_3d():
