@@ -35,10 +35,25 @@ namespace jgb {
 // scalar helpers
 
 // a + b rounded to nearest even, issued as fma(a, 1, b): the product a * 1 is
-// exact, so the result is bit-identical to __dadd_rn(a, b) for every input,
-// and on GB300 the FMA form issues faster than DADD (about 1.9 versus 1.6 per
-// clock per SM, measured).
-__device__ __forceinline__ double dadd(double a, double b) { return __fma_rn(a, 1.0, b); }
+// exact, so the result is bit-identical to __dadd_rn(a, b) for every input.
+// On GB300 the FMA issues faster than the FP64 add (about 1.9 versus 1.55 per
+// clock per SM, measured).  It is written in PTX because the compiler turns
+// fma(a, 1.0, b) in C++ back into an add.
+__device__ __forceinline__ double dadd(double a, double b) {
+  double r;
+  asm("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(r) : "d"(a), "d"(b));
+  return r;
+}
+
+// The rare-case paths behind the warp votes below are out-of-line calls: the
+// compiler would otherwise compute them for every point and select afterwards,
+// an FP64 multiply (or a whole FP64 division) per point on a pipe that is the
+// bottleneck.
+__device__ __noinline__ double slow_quarter(double t) { return __dmul_rn(t, 0.25); }
+__device__ __noinline__ double slow_sixth(double t) { return __ddiv_rn(t, 6.0); }
+__device__ __noinline__ double slow_times4(double c) { return __dmul_rn(4.0, c); }
+__device__ __noinline__ double slow_f2d(float v) { return (double)v; }
+__device__ __noinline__ float slow_d2f(double v) { return __double2float_rn(v); }
 
 // t / 4, exact: exponent decrement on the integer pipe, FP64 multiply only when
 // some lane of the warp needs it (zero, subnormal, inf/NaN).
@@ -47,7 +62,7 @@ __device__ __forceinline__ double div_2d(double t) {
   const bool fast = quarter_fast(b);
   double q = quarter_bits(b);
   if (!__all_sync(FULL_MASK, fast)) {
-    if (!fast) q = __dmul_rn(t, 0.25);
+    if (!fast) q = slow_quarter(t);
   }
   return q;
 }
@@ -59,7 +74,7 @@ __device__ __forceinline__ double div_3d(double t) {
   const bool fast = sixth_fast(b);
   double q = sixth_bits(b);
   if (!__all_sync(FULL_MASK, fast)) {
-    if (!fast) q = __ddiv_rn(t, 6.0);
+    if (!fast) q = slow_sixth(t);
   }
   return q;
 }
@@ -224,15 +239,19 @@ __device__ __forceinline__ float4 ldf4(const __nv_bfloat16* p) {
 // twod_x, dadd_int), these must be called by all 32 lanes together.
 __device__ __forceinline__ double f2d(float v) {
   bool ok;
-  const double r = f64_from_bits(f32_to_f64_bits(__float_as_uint(v), ok));
-  if (__all_sync(FULL_MASK, ok)) return r;
-  return ok ? r : (double)v;
+  double r = f64_from_bits(f32_to_f64_bits(__float_as_uint(v), ok));
+  if (!__all_sync(FULL_MASK, ok)) {
+    if (!ok) r = slow_f2d(v);
+  }
+  return r;
 }
 __device__ __forceinline__ float d2f(double v) {
   bool ok;
-  const float r = __uint_as_float(f64_to_f32_bits(f64_bits(v), ok));
-  if (__all_sync(FULL_MASK, ok)) return r;
-  return ok ? r : __double2float_rn(v);
+  float r = __uint_as_float(f64_to_f32_bits(f64_bits(v), ok));
+  if (!__all_sync(FULL_MASK, ok)) {
+    if (!ok) r = slow_d2f(v);
+  }
+  return r;
 }
 // (2d) x of the residual: 4x exactly on the integer pipe in 2D, a rounded
 // FP64 product 6x in 3D.
@@ -240,9 +259,11 @@ template <int DIM>
 __device__ __forceinline__ double twod_x(double c) {
   if constexpr (DIM == 2) {
     bool ok;
-    const double r = f64_from_bits(times4_bits(f64_bits(c), ok));
-    if (__all_sync(FULL_MASK, ok)) return r;
-    return ok ? r : __dmul_rn(4.0, c);
+    double r = f64_from_bits(times4_bits(f64_bits(c), ok));
+    if (!__all_sync(FULL_MASK, ok)) {
+      if (!ok) r = slow_times4(c);
+    }
+    return r;
   } else {
     return __dmul_rn(6.0, c);
   }
@@ -377,11 +398,14 @@ __device__ __forceinline__ void push_targets(PushTargets& T, const BlockDev& B, 
 
 // a + b for every lane, on the integer pipe when every lane of the warp is on
 // the software fast path (exact_f64.cuh), else on the FP64 pipe.
+__device__ __noinline__ double slow_add(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double dadd_int(double a, double b) {
   bool ok;
-  const double r = f64_from_bits(add_bits(f64_bits(a), f64_bits(b), ok));
-  if (__all_sync(FULL_MASK, ok)) return r;
-  return ok ? r : dadd(a, b);
+  double r = f64_from_bits(add_bits(f64_bits(a), f64_bits(b), ok));
+  if (!__all_sync(FULL_MASK, ok)) {
+    if (!ok) r = slow_add(a, b);
+  }
+  return r;
 }
 
 // EMU: how many of the seven FP64 additions of a warp step run on the
