@@ -754,6 +754,8 @@ __device__ __forceinline__ void stv(__nv_bfloat16* p, const float (&v)[V], int n
   }
 }
 
+// Points per lane of the low-precision sweeps: 4 float or 8 bfloat16 (16-byte
+// loads of e).
 template <typename TE>
 __host__ __device__ constexpr int low_vpl() {
   return sizeof(TE) == 2 ? 8 : 4;
@@ -778,16 +780,16 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
   const int l = lane & (L - 1);
   const int y = DIM == 3 ? it.y0 + (lane >> lgL) : it.y0;
   const bool row_ok = DIM == 2 || y < B.by;
-  const Geo<DIM> G(B, row_ok ? y : B.by - 1);
+  const Geo<DIM> G(B, DIM == 2 ? y : (row_ok ? y : B.by - 1));
   const int bx = B.bx;
   const int xs = it.seg * (L * V);
   const int x = xs + V * l;
-  const int nvalid = row_ok ? bx - x : 0;  // > 0 when the lane holds points
+  const int nvalid = DIM == 2 ? bx - x : (row_ok ? bx - x : 0);  // > 0 when the lane holds points
   const bool any = nvalid > 0;
   const int64_t gW = B.xoff;
   const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
   PushTargets T;
-  if constexpr (PUSH) push_targets<DIM>(T, B, blocks, row_ok ? y : B.by - 1);
+  if constexpr (PUSH) push_targets<DIM>(T, B, blocks, DIM == 2 ? y : (row_ok ? y : B.by - 1));
 
   const int m0 = DIM == 2 ? it.y0 : it.z0;
   const int mend = m0 + it.n;
@@ -799,6 +801,82 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
       ldv<COH, V>(es + G.line(m0 - 1) + x, p);
       ldv<COH, V>(es + G.line(m0) + x, c);
     }
+  }
+  if constexpr (DIM == 3 && !FIRST && V == 4) {
+    // Float in 3D: every load line m + 1 needs (r, e of line m + 2, the rows
+    // y - 1 and y + 1, the edge scalars) is issued before line m is computed,
+    // so a warp keeps two lines of loads in flight (measured 1.24x at 512^3;
+    // with 8 bfloat16 per lane the second line's registers cost more
+    // occupancy than the prefetch gains, and 4 per lane is slower still).
+    struct Ln {
+      float r[V], n[V], sa[V], sb[V];
+      float wv, ev, ge;
+    };
+    auto fetch = [&](int m, Ln& q) {
+      const int64_t lc = G.line(m);
+      const int col = G.col(m);
+#pragma unroll
+      for (int k = 0; k < V; ++k) q.r[k] = q.n[k] = q.sa[k] = q.sb[k] = 0.f;
+      q.wv = q.ev = q.ge = 0.f;
+      if (any) {
+        ldv<false, V>(rr + lc + x, q.r);
+        ldv<COH, V>(es + G.line(m + 1) + x, q.n);
+        ldv<COH, V>(es + lc - G.side + x, q.sa);
+        ldv<COH, V>(es + lc + G.side + x, q.sb);
+        if (l == 0) q.wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
+        if (l == L - 1 && x + V < bx) q.ev = ldf<COH>(es + lc + x + V);
+        if (nvalid <= V) q.ge = ldf<COH>(es + gE + col);
+      }
+    };
+    Ln cur;
+    fetch(m0, cur);
+    for (int m = m0; m < mend; ++m) {
+      const int64_t lc = G.line(m);
+      const int col = G.col(m);
+      Ln nx;
+      const bool more = m + 1 < mend;
+      if (more) fetch(m + 1, nx);
+      float wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1, L);
+      if (l == 0) wv = cur.wv;
+      float ev = __shfl_down_sync(FULL_MASK, c[0], 1, L);
+      if (l == L - 1 && x + V < bx) ev = cur.ev;
+      float o[V];
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        const float west = k == 0 ? wv : c[k - 1];
+        float east = k == V - 1 ? ev : c[k + 1];
+        if (k + 1 == nvalid) east = cur.ge;  // the block's last point takes the ghost
+        float t = __fadd_rn(__fadd_rn(west, p[k]), __fadd_rn(east, cur.n[k]));
+        t = __fadd_rn(t, __fadd_rn(cur.sa[k], cur.sb[k]));
+        t = __fadd_rn(t, cur.r[k]);
+        o[k] = jdivf<DIM>(t);
+      }
+      if (any) {
+        stv<V>(ed + lc + x, o, nvalid);
+        if constexpr (PUSH) {
+          if (m == 0 && T.lo_line >= 0) stv<V>(ed + T.lo_line + x, o, nvalid);
+          if (m == G.extent - 1 && T.hi_line >= 0) stv<V>(ed + T.hi_line + x, o, nvalid);
+          if (T.lo_side >= 0) stv<V>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
+          if (T.hi_side >= 0) stv<V>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
+          if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o[0]);
+          if (nvalid <= V && T.e_col >= 0) {
+            float last = o[0];
+#pragma unroll
+            for (int k = 1; k < V; ++k)
+              if (k == nvalid - 1) last = o[k];
+            ed[T.e_col + col] = from_f<TE>(last);
+          }
+        }
+      }
+      if (!more) break;
+#pragma unroll
+      for (int k = 0; k < V; ++k) {
+        p[k] = c[k];
+        c[k] = cur.n[k];
+      }
+      cur = nx;
+    }
+    return;
   }
   for (int m = m0; m < mend; ++m) {
     const int64_t lc = G.line(m);
@@ -824,11 +902,21 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
           ldv<COH, V>(es + lc + G.side + x, sb);
         }
       }
-      // west of point 0, east of point V-1 (shuffles stay inside the row's L lanes)
-      float wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1, L);
-      if (l == 0 && any) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
-      float ev = __shfl_down_sync(FULL_MASK, c[0], 1, L);
-      if (l == L - 1 && any && x + V < bx) ev = ldf<COH>(es + lc + x + V);
+      // west of point 0, east of point V-1 (in 3D the shuffles stay inside
+      // the row's L lanes; the 2D forms are written apart, as the compiler
+      // schedules the plain ones measurably better)
+      float wv, ev;
+      if constexpr (DIM == 2) {
+        wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
+        if (lane == 0) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
+        ev = __shfl_down_sync(FULL_MASK, c[0], 1);
+        if (lane == 31 && x + V < bx) ev = ldf<COH>(es + lc + x + V);
+      } else {
+        wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1, L);
+        if (l == 0 && any) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
+        ev = __shfl_down_sync(FULL_MASK, c[0], 1, L);
+        if (l == L - 1 && any && x + V < bx) ev = ldf<COH>(es + lc + x + V);
+      }
       float ge = 0.f;
       if (any && nvalid <= V) ge = ldf<COH>(es + gE + col);
 #pragma unroll
@@ -871,10 +959,22 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
   }
 }
 
+// Launch bounds measured per form: bfloat16 in 2D runs best held to 3 CTAs
+// per SM, float in 2D best with no occupancy hint at all (k_low_free).
 template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR>
 __global__ void __launch_bounds__(kThreads, DIM == 2 && sizeof(TE) == 2 ? 3 : 1)
 k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
       const SolveDev* __restrict__ solves, int epar) {
+  const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
+  if (w >= nitems) return;
+  const WorkItem it = items[w];
+  if (!solves[blocks[it.block].solve].active) return;
+  low_item<DIM, FIRST, PUSH, TE, TR, false>(it, blocks, solves, epar);
+}
+template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads)
+k_low_free(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
+           const SolveDev* __restrict__ solves, int epar) {
   const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (w >= nitems) return;
   const WorkItem it = items[w];
@@ -1470,7 +1570,15 @@ template <int DIM, typename TE, typename TR>
 static int low_typed(const Tables& t, int epar, bool first, bool push, cudaStream_t s) {
   const dim3 g(grid_of(t.nlo, kWarps)), b(kThreads);
   if (t.nlo == 0) return 0;
-  if (first) {
+  if constexpr (DIM == 2 && sizeof(TE) == 4) {
+    if (first) {
+      if (push) k_low_free<DIM, true, true, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+      else k_low_free<DIM, true, false, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+    } else {
+      if (push) k_low_free<DIM, false, true, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+      else k_low_free<DIM, false, false, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+    }
+  } else if (first) {
     if (push) k_low<DIM, true, true, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
     else k_low<DIM, true, false, TE, TR><<<g, b, 0, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
   } else {
