@@ -50,11 +50,11 @@ FP64_ADDS_PER_LUP = {2: 3.0, 3: 5.0}
 BYTES_PER_LUP = {"f64": 24.0, "f32_refine": 12.0, "bf16_refine": 8.0}
 METRIC = "Jacobi GLUP/s & % HBM roofline, mixed vs FP64 at 1e-8 resid; p99 solve ms"
 # DRAM bytes (read + write) per lattice update of the 2D FP64 sweep kernel
-# (k_f64_march), from an ncu capture of a 4096^2 launch; traffic grows with
-# the points, so a full launch is this times its points.  None until that
-# capture exists for the kernel as built (it must be retaken whenever the
-# kernel changes).
-F64_SWEEP_DRAM_BYTES_PER_LUP = None
+# (k_f64_march), from the ncu capture summarised in
+# profiles/sweep_f64_poisson2d_4096.md (270.3 MB read + 106.3 MB written for
+# 16.8 M updates); traffic grows with the points, so a full launch is this
+# times its points.  Must be retaken whenever that kernel changes.
+F64_SWEEP_DRAM_BYTES_PER_LUP = (270.267648e6 + 106.273280e6) / (4096 * 4096)
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--emu", type=int, default=-1, help="FP64 additions per warp step on the integer pipe (0, 2, 3)")
     ap.add_argument("--tma", type=int, default=-1, help="2D inner sweeps staged by bulk async copies (0/1)")
     ap.add_argument("--march", type=int, default=-1, help="2D FP64 sweeps over march items (0/1)")
+    ap.add_argument("--outer-split", type=int, default=-1, help="3D outer step in two passes (0/1)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -249,6 +250,8 @@ def time_form(p, form, sweeps, args, world, stream, sampler=None):
         opts["march"] = args.march
     if form != "f64" and args.tma >= 0:
         opts["tma"] = args.tma
+    if form != "f64" and args.outer_split >= 0:
+        opts["outer_split"] = args.outer_split
     s = J.Solver(p.dims, p.block, dtype=form, faces=p.faces, source=p.source, x0=p.x0,
                  check_every=CHECK_EVERY, refine_period=CHECK_EVERY, profile=1, **opts)
 

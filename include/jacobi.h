@@ -171,7 +171,12 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
  *                    FP64 sweep moved to the integer pipe (bit-identical;
  *                    slower on GB300, kept for measurement)
  *   "tma"            1: 2D inner sweeps after the first of a refinement step
- *                    stage their lines in shared memory by bulk async copies */
+ *                    stage their lines in shared memory by bulk async copies
+ *   "outer_split"    1 (default): in 3D the refinement's outer step runs as
+ *                    x_new = x + e over the whole block layout, then the
+ *                    residual pass on x_new (fewer FP64 operations per point
+ *                    than forming x + e for every neighbour load); 0: one
+ *                    fused pass */
 jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value);
 jacobi_status jacobi_get_option(jacobi_t ctx, const char* key, int64_t* value);
 

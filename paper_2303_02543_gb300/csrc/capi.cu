@@ -247,6 +247,7 @@ static int64_t* option_slot(Options& o, const char* key) {
   if (!strcmp(key, "emu_adds")) return &o.emu_adds;
   if (!strcmp(key, "tma")) return &o.tma;
   if (!strcmp(key, "march")) return &o.march;
+  if (!strcmp(key, "outer_split")) return &o.outer_split;
   return nullptr;
 }
 
@@ -260,7 +261,7 @@ jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value) {
   if (k == "check_every" || k == "rows_f64" || k == "rows_low") require(value >= 1, k + " must be >= 1");
   if (k == "refine_period") require(value >= 1 && value <= 4096, "refine_period must be in [1, 4096]");
   if (k == "halo" || k == "profile" || k == "schedule" || k == "graph" || k == "poison_wait" || k == "autotune" ||
-      k == "tma" || k == "march")
+      k == "tma" || k == "march" || k == "outer_split")
     require(value == 0 || value == 1, k + " must be 0 or 1");
   if (k == "spin_limit") require(value >= 0 && value <= 0x7fffffff, "spin_limit must be in [0, 2^31)");
   if (k == "emu_adds") require(value == 0 || value == 2 || value == 3, "emu_adds must be 0, 2 or 3");

@@ -247,6 +247,7 @@ void Workset::push_solve_dev(SolveHost& s) {
   d.rss = d_rss_ + s.slot;
   d.ticket = d_ticket_ + s.slot;
   d.nparts = s.nparts;
+  d.elems = s.elems;
   d.part_row = s.part_row;
   d.ny = (int32_t)s.spec.n[1];
   d.ndim = s.spec.ndim;
@@ -689,7 +690,15 @@ void Workset::refine_outer() {
   const Tables t = tables();
   const bool push = opt.halo == 0;
   prof_begin(kProfOuter);
-  LAUNCH(launch_refine_outer(t, epar_last_, push, low(), r_bf16_, cur_), "refine outer");
+  if (ndim_ == 3 && opt.outer_split) {
+    int64_t max_elems = 0;
+    for (auto* s : solves_)
+      if (s) max_elems = std::max<int64_t>(max_elems, s->elems);
+    LAUNCH(launch_refine_outer_split(t, capacity_, max_elems, epar_last_, low(), r_bf16_, cur_),
+           "refine outer (split)");
+  } else {
+    LAUNCH(launch_refine_outer(t, epar_last_, push, low(), r_bf16_, cur_), "refine outer");
+  }
   prof_end(kProfOuter);
   if (!push) {
     prof_begin(kProfHalo);

@@ -114,6 +114,7 @@ struct Options {
   int64_t emu_adds = 0;      // FP64 sweep: additions per warp step done on the integer pipe (0, 2, 3)
   int64_t tma = 0;           // 2D inner sweeps: stage lines in shared memory with bulk async copies
   int64_t march = 1;         // FP64 sweeps without a residual: one warp computes all segments of a line range
+  int64_t outer_split = 1;   // 3D outer step as x += e over the layout, then the residual pass
 };
 
 // Outcome of one solve inside solve_all.

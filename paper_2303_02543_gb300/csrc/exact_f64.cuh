@@ -195,4 +195,26 @@ JGB_HD uint64_t times4_bits(uint64_t b, bool& ok) {
   return b + (2ull << 52);
 }
 
+// 6 x rounded to nearest-even, for normal x with 6x normal and for zeros
+// (ok false otherwise).  x = M 2^(e-1075) with the 53-bit significand M, so
+// 6x = P 2^(e-1074) with P = 3M in [1.5 2^53, 1.5 2^54): P keeps 54 or 55
+// bits, of which the lowest sh = 1 or 2 are dropped with round-to-nearest,
+// ties to even; the biased exponent of the result is e + 1 + sh, and a carry
+// out of the significand moves into the exponent field by itself.
+JGB_HD uint64_t times6_bits(uint64_t b, bool& ok) {
+  const uint32_t e = (uint32_t)(b >> 52) & 0x7FFu;
+  if ((b & 0x7FFFFFFFFFFFFFFFull) == 0) {
+    ok = true;
+    return b;
+  }
+  ok = e - 1u < 2042u;
+  const uint64_t M = (b & 0x000FFFFFFFFFFFFFull) | 0x0010000000000000ull;
+  const uint64_t P = M * 3u;
+  const uint32_t sh = 1u + (uint32_t)(P >> 54);
+  const uint64_t rem = P & ((1ull << sh) - 1u), half = 1ull << (sh - 1u);
+  uint64_t q = P >> sh;
+  q += (uint64_t)((rem > half) | ((rem == half) & (uint32_t)(q & 1u)));
+  return (b & 0x8000000000000000ull) + ((uint64_t)(e + sh) << 52) + q;
+}
+
 }  // namespace jgb

@@ -77,6 +77,7 @@ struct SolveDev {
   double* rss;        // [0] = sum of squares written by the reduction
   uint32_t* ticket;   // reduction ticket
   int64_t nparts;     // residual partial slots
+  int64_t elems;      // elements of each layout array (x, f, e, r)
   int32_t part_row;   // partial slots per grid row
   int32_t ny;         // grid rows along y (for the partial row index)
   int32_t ndim;
@@ -168,6 +169,12 @@ int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, 
 // by bulk asynchronous copies; a timed-out wait sets ctl->status bit 1.
 int launch_sweep_low_tma(const Tables& t, int epar, bool push, int low, bool r_bf16, void* stream);
 int launch_refine_outer(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream);
+// The outer step in two passes: x[phase^1] = x[phase] + e over every element
+// of the layout (ghosts included: e's ghosts hold the neighbours' values and
+// zero on the domain faces), then r = b - A x[phase^1] with no x write.
+// max_elems: the largest `elems` of the solves.
+int launch_refine_outer_split(const Tables& t, int nslots, int64_t max_elems, int epar_last, int low, bool r_bf16,
+                              void* stream);
 int launch_halo_pack(const Tables& t, int which, int par, int low, void* stream);
 int launch_halo_unpack(const Tables& t, int which, int par, int low, void* stream);
 int launch_reduce(const Tables& t, void* stream);

@@ -52,6 +52,7 @@ __device__ __forceinline__ double dadd(double a, double b) {
 __device__ __noinline__ double slow_quarter(double t) { return __dmul_rn(t, 0.25); }
 __device__ __noinline__ double slow_sixth(double t) { return __ddiv_rn(t, 6.0); }
 __device__ __noinline__ double slow_times4(double c) { return __dmul_rn(4.0, c); }
+__device__ __noinline__ double slow_times6(double c) { return __dmul_rn(6.0, c); }
 __device__ __noinline__ double slow_f2d(float v) { return (double)v; }
 __device__ __noinline__ float slow_d2f(double v) { return __double2float_rn(v); }
 
@@ -188,7 +189,9 @@ struct PushTargets {
 };
 
 // MODE of the FP64 kernel
-enum { kModeSweep = 0, kModeResid = 1, kModeOuter = 2 };
+// kModeOuterR: the residual pass of the split outer step (reads x_new, stores
+// r in the low type and the partials; writes no x)
+enum { kModeSweep = 0, kModeResid = 1, kModeOuter = 2, kModeOuterR = 3 };
 
 // Load policies.  COH = false: read-only path (__ldg), valid when nothing
 // writes the array during the launch.  COH = true: L2-only loads (__ldcg),
@@ -253,8 +256,9 @@ __device__ __forceinline__ float d2f(double v) {
   }
   return r;
 }
-// (2d) x of the residual: 4x exactly on the integer pipe in 2D, a rounded
-// FP64 product 6x in 3D.
+// (2d) x of the residual on the integer pipe: 4x exactly in 2D, 6x rounded
+// to nearest-even in 3D (exact_f64.cuh); the FP64 product only when a lane
+// leaves the fast range.
 template <int DIM>
 __device__ __forceinline__ double twod_x(double c) {
   if constexpr (DIM == 2) {
@@ -265,7 +269,12 @@ __device__ __forceinline__ double twod_x(double c) {
     }
     return r;
   } else {
-    return __dmul_rn(6.0, c);
+    bool ok;
+    double r = f64_from_bits(times6_bits(f64_bits(c), ok));
+    if (!__all_sync(FULL_MASK, ok)) {
+      if (!ok) r = slow_times6(c);
+    }
+    return r;
   }
 }
 
@@ -424,7 +433,8 @@ template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, bo
 __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __restrict__ blocks,
                                          const SolveDev* __restrict__ solves, int kpar, int epar,
                                          const double* rd = nullptr, double* wr = nullptr) {
-  constexpr bool WRITE = MODE != kModeResid;
+  constexpr bool WRITE = MODE != kModeResid && MODE != kModeOuterR;
+  constexpr bool STORE_R = MODE == kModeOuter || MODE == kModeOuterR;
   const int lane = threadIdx.x & 31;
   const BlockDev B = blocks[it.block];
   const SolveDev* S = solves + B.solve;
@@ -435,7 +445,7 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   src.apply = MODE == kModeOuter && S->apply_e;
   double* __restrict__ xd = S->x[par ^ 1];
   const double* __restrict__ f = S->f;
-  TR* __restrict__ rout = MODE == kModeOuter ? reinterpret_cast<TR*>(S->r) : nullptr;
+  TR* __restrict__ rout = STORE_R ? reinterpret_cast<TR*>(S->r) : nullptr;
 
   const int y = it.y0;  // 3D: the fixed row
   const Geo<DIM> G(B, y);
@@ -609,10 +619,11 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
         }
       }
     }
-    if constexpr (RESID || MODE == kModeOuter) {
-      const double r0 = __dsub_rn(t0, twod_x<DIM>(c0));
-      const double r1 = __dsub_rn(t1, twod_x<DIM>(c1));
-      if constexpr (MODE == kModeOuter) {
+    if constexpr (RESID || STORE_R) {
+      // t - (2d) x as fma(t, 1, -(2d) x): the same rounding as the subtraction
+      const double r0 = dadd(t0, -twod_x<DIM>(c0));
+      const double r1 = dadd(t1, -twod_x<DIM>(c1));
+      if constexpr (STORE_R) {
         const float rf0 = d2f(r0), rf1 = d2f(r1);
         if (v1) {
           store_r<TR>(rout + lc + x, rf0);
@@ -959,10 +970,10 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
   }
 }
 
-// Launch bounds measured per form: bfloat16 in 2D runs best held to 3 CTAs
+// Launch bounds measured per form: bfloat16 in 2D runs best held to 4 CTAs
 // per SM, float in 2D best with no occupancy hint at all (k_low_free).
 template <int DIM, bool FIRST, bool PUSH, typename TE, typename TR>
-__global__ void __launch_bounds__(kThreads, DIM == 2 && sizeof(TE) == 2 ? 3 : 1)
+__global__ void __launch_bounds__(kThreads, DIM == 2 && sizeof(TE) == 2 ? 4 : 1)
 k_low(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
       const SolveDev* __restrict__ solves, int epar) {
   const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
@@ -1608,6 +1619,60 @@ static int outer_typed(const Tables& t, int epar_last, bool push, cudaStream_t s
   if (push) k_f64<DIM, kModeOuter, true, true, TE, TR><<<g, b, 0, s>>>(t.w64, t.n64, 0, t.blocks, t.solves, epar_last);
   else k_f64<DIM, kModeOuter, false, true, TE, TR><<<g, b, 0, s>>>(t.w64, t.n64, 0, t.blocks, t.solves, epar_last);
   return (int)cudaGetLastError();
+}
+
+// x[phase^1] = x[phase] + e (or a copy while the solve has no correction
+// yet) over every element of each active solve's layout; blockIdx.y = slot.
+template <typename TE>
+__global__ void __launch_bounds__(kThreads)
+k_apply_e(SolveDev* __restrict__ solves, int epar) {
+  const SolveDev* S = solves + blockIdx.y;
+  if (!S->active) return;
+  const int lane = threadIdx.x & 31;
+  const double* __restrict__ xs = S->x[S->phase & 1];
+  double* __restrict__ xd = S->x[(S->phase & 1) ^ 1];
+  const TE* __restrict__ e = reinterpret_cast<const TE*>(S->e[epar]);
+  const bool apply = S->apply_e != 0;
+  const int64_t n = S->elems;  // a multiple of 32
+  const int64_t wstride = (int64_t)gridDim.x * kWarps * 64;
+  for (int64_t w0 = ((int64_t)blockIdx.x * kWarps + (threadIdx.x >> 5)) * 64; w0 < n; w0 += wstride) {
+    const int64_t i = w0 + 2 * lane;
+    const bool valid = i < n;
+    double2 v = make_double2(0.0, 0.0);
+    float ea = 0.f, eb = 0.f;
+    if (valid) {
+      v = *reinterpret_cast<const double2*>(xs + i);
+      if (apply) {
+        ea = ldf<false>(e + i);
+        eb = ldf<false>(e + i + 1);
+      }
+    }
+    if (apply) {  // uniform
+      v.x = dadd(v.x, f2d(ea));
+      v.y = dadd(v.y, f2d(eb));
+    }
+    if (valid) *reinterpret_cast<double2*>(xd + i) = v;
+  }
+}
+
+template <typename TE, typename TR>
+static int outer_split_typed(const Tables& t, int nslots, int64_t max_elems, int epar_last, cudaStream_t s) {
+  if (t.n64 == 0 || nslots <= 0 || max_elems <= 0) return 0;
+  const int64_t per_cta = (int64_t)kWarps * 64;
+  const unsigned gx = (unsigned)std::min<int64_t>((max_elems + per_cta - 1) / per_cta, 4096);
+  k_apply_e<TE><<<dim3(gx, (unsigned)nslots), kThreads, 0, s>>>(t.solves, epar_last);
+  k_f64<3, kModeOuterR, false, true, float, TR><<<grid_of(t.n64, kWarps), kThreads, 0, s>>>(t.w64, t.n64, 1, t.blocks,
+                                                                                          t.solves, 0);
+  return (int)cudaGetLastError();
+}
+
+int launch_refine_outer_split(const Tables& t, int nslots, int64_t max_elems, int epar_last, int low, bool r_bf16,
+                              void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.ndim != 3 || nslots > 65535) return (int)cudaErrorInvalidValue;
+  if (low == kLowF32) return outer_split_typed<float, float>(t, nslots, max_elems, epar_last, s);
+  if (r_bf16) return outer_split_typed<__nv_bfloat16, __nv_bfloat16>(t, nslots, max_elems, epar_last, s);
+  return outer_split_typed<__nv_bfloat16, float>(t, nslots, max_elems, epar_last, s);
 }
 
 template <int DIM>

@@ -29,7 +29,7 @@ static void check_add(double x, double y) {
   }
 }
 
-static long conv_checked = 0;
+static long conv_checked = 0, x6_fast = 0;
 
 static void check_conv(double d, float f) {
   bool ok;
@@ -54,6 +54,12 @@ static void check_conv(double d, float f) {
     if (bad < 10) std::printf("x4 mismatch %a\n", d);
     ++bad;
   }
+  const uint64_t q6 = times6_bits(f64_bits(d), ok);
+  if (ok && q6 != f64_bits(d * 6.0)) {
+    if (bad < 10) std::printf("x6 mismatch %a: %a vs %a\n", d, f64_from_bits(q6), d * 6.0);
+    ++bad;
+  }
+  if (ok) ++x6_fast;
 }
 
 static void check(double t) {
@@ -137,7 +143,17 @@ int main(int argc, char** argv) {
   check_conv(0.0, 0.0f);
   check_conv(-0.0, -0.0f);
   check_conv(3.4028235677973366e38, 3.4028235e38f);  // rounds past FLT_MAX -> not fast
-  std::printf("conversions %ld\n", conv_checked);
+  // x6 at the edges of its fast range: largest exponents, smallest normals
+  for (uint64_t e = 2038; e <= 2046; ++e)
+    for (long k = 0; k < 2000; ++k) {
+      const double d = f64_from_bits((e << 52) | (g() & 0x000FFFFFFFFFFFFFull));
+      check_conv(d, 0.0f);
+      check_conv(-d, 0.0f);
+    }
+  for (uint64_t e = 1; e <= 4; ++e)
+    for (long k = 0; k < 2000; ++k) check_conv(f64_from_bits((e << 52) | (g() & 0x000FFFFFFFFFFFFFull)), 0.0f);
+  check_conv(f64_from_bits(0x7FEFFFFFFFFFFFFFull), 0.0f);
+  std::printf("conversions %ld (x6 fast %ld)\n", conv_checked, x6_fast);
   std::printf("checked %ld mismatches %ld\n", checked, bad);
   return bad != 0;
 }

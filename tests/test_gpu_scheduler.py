@@ -152,3 +152,26 @@ def test_autotune_keeps_results_and_writes_cache(tmp_path, monkeypatch):
         st4, sw4, _ = s.solve(1e-3, 10 ** 5)
         st5, x5, sw5, _ = oracle.solve(p.dims, p.faces, p.source, None, 1e-3, 10 ** 5, 10)
         assert sw4 == sw5 and np.array_equal(s.field(), x5)
+
+
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16r16_refine", True, True)])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_split_outer_step_3d_bit_exact(dtype, e16, r16, graph):
+    """The 3D outer step as x + e over the layout then the residual pass gives
+    the bits of the fused pass and of the oracle, alone and in a batch of
+    uneven 3D solves (several slots of the apply kernel's grid)."""
+    probs = [inputs.make_problem(d, b, 90 + i, boundary="uniform", source="normal", x0="zero")
+             for i, (d, b) in enumerate([((20, 17, 13), (8, 9, 5)), ((9, 30, 11), (9, 16, 4)), ((33, 5, 7), (32, 5, 7))])]
+    fields = {}
+    for split in (0, 1):
+        with J.Batch(probs, dtype=dtype, refine_period=10, outer_split=split, graph=graph) as b:
+            st, res = b.solve(1e-8, 10 ** 6)
+            assert st == J.OK
+            fields[split] = ([b.field(i) for i in range(len(probs))], [r[1] for r in res])
+    assert fields[0][1] == fields[1][1]
+    for i, p in enumerate(probs):
+        assert np.array_equal(fields[0][0][i], fields[1][0][i])
+        st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, 10,
+                                                 e_bf16=e16, r_bf16=r16)
+        assert fields[1][1][i] == sw_o
+        assert np.array_equal(fields[1][0][i], x_o)
