@@ -170,8 +170,10 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
  *   "emu_adds"       0 (default), 2 or 3: FP64 additions per warp step of the
  *                    FP64 sweep moved to the integer pipe (bit-identical;
  *                    slower on GB300, kept for measurement)
- *   "tma"            1: 2D inner sweeps after the first of a refinement step
- *                    stage their lines in shared memory by bulk async copies
+ *   "tma"            1: inner sweeps after the first of a refinement step
+ *                    stage the lines they read in shared memory by bulk async
+ *                    copies (2D: the warp's line of e and r; 3D: its rows of
+ *                    e with the rows above and below, and of r)
  *   "outer_split"    1 (default): in 3D the refinement's outer step runs as
  *                    x_new = x + e over the whole block layout, then the
  *                    residual pass on x_new (fewer FP64 operations per point

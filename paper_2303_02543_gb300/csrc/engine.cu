@@ -306,6 +306,7 @@ void Workset::rebuild_tables() {
   table_allocs_.clear();
   std::vector<BlockDev> blocks;
   std::vector<WorkItem> w64, wlo, wm;
+  int estage = 0;
   std::vector<CtaTask> t64, tlo;
   std::vector<FaceItem> faces;
   std::vector<RedItem> red;
@@ -339,12 +340,15 @@ void Workset::rebuild_tables() {
     mlen = (int)std::min<int64_t>(std::max<int64_t>((mlines + target - 1) / target, 8), kMarchLines);
     while (mlen < kMarchLines && count(mlen) > target) ++mlen;
   }
+  tabled_points_ = 0;
   for (int slot = 0; slot < capacity_; ++slot) {
     SolveHost* s = solves_[slot];
     if (!s) continue;
     const int base = (int)blocks.size();
     face_base_[slot] = (int)faces.size();
     row_base_[slot] = (int)rows.size();
+    if (compact_ && !s->active) continue;  // retired inside solve_all: no work items
+    tabled_points_ += s->points();
     for (size_t b = 0; b < s->blocks.size(); ++b) {
       BlockDev B = s->blocks[b];
       B.solve = slot;
@@ -385,6 +389,8 @@ void Workset::rebuild_tables() {
         const int v = low() == kLowBF16 ? kSegLow16 / 32 : kSegLow / 32;
         const int lg = ndim_ == 3 ? low_lanes_log2(B.bx, v) : 5;
         B.ntlo = items(wlo, tlo, v << lg, rlo, 32 >> lg);
+        // staged 3D sweep: e elements per stage = (rows + 2) x points per row
+        estage = std::max(estage, ((32 >> lg) + 2) * (v << lg));
       } else {
         B.ntlo = 0;
       }
@@ -423,6 +429,7 @@ void Workset::rebuild_tables() {
   }
   n64_ = (int)w64.size();
   nm_ = (int)wm.size();
+  estage_ = estage;
   nlo_ = (int)wlo.size();
   nt64_ = (int)t64.size();
   ntlo_ = (int)tlo.size();
@@ -473,6 +480,7 @@ Tables Workset::solve_tables(const SolveHost& s) const {
 }
 
 void Workset::scatter(int slot, const double* dense, int which, int on_device) {
+  if (tables_dirty_) rebuild_tables();
   SolveHost* s = solve(slot);
   const int64_t npts = s->points();
   const double* src = dense;
@@ -490,6 +498,7 @@ void Workset::scatter(int slot, const double* dense, int which, int on_device) {
 }
 
 void Workset::gather(int slot, double* dense, int on_device) {
+  if (tables_dirty_) rebuild_tables();
   SolveHost* s = solve(slot);
   const int64_t npts = s->points();
   double* dst = dense;
@@ -721,11 +730,14 @@ void Workset::refine_inner(int64_t k) {
     LAUNCH(launch_persist_low(t, (int)k, low(), r_bf16_, cur_), "persistent sweep low");
     prof_end(kProfSweepLow);
   } else {
-    const bool tma = opt.tma && ndim_ == 2;
+    const bool tma = opt.tma != 0;
     for (int64_t j = 0; j < k; ++j) {
       const int epar = (int)(j & 1);
       prof_begin(kProfSweepLow);
-      if (tma && j > 0) LAUNCH(launch_sweep_low_tma(t, epar, push, low(), r_bf16_, cur_), "sweep low (staged)");
+      if (tma && j > 0 && ndim_ == 2)
+        LAUNCH(launch_sweep_low_tma(t, epar, push, low(), r_bf16_, cur_), "sweep low (staged)");
+      else if (tma && j > 0)
+        LAUNCH(launch_sweep_low_stage3(t, epar, push, low(), r_bf16_, estage_, cur_), "sweep low (staged, 3D)");
       else LAUNCH(launch_sweep_low(t, epar, j == 0, push, low(), r_bf16_, cur_), "sweep low");
       prof_end(kProfSweepLow);
       if (!push) {
@@ -867,7 +879,18 @@ void Workset::solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>&
       ctl[k] = ref ? 4 : 2;
       retire = true;
     }
-    if (retire) apply_slot_ctl(ctl);
+    if (retire) {
+      apply_slot_ctl(ctl);
+      // once the retired solves hold most of the tabled points, launch only
+      // the active ones (the tables and graphs are rebuilt at the next step)
+      int64_t live_pts = 0;
+      for (int k : slots)
+        if (!res[k].done) live_pts += solves_[k]->points();
+      if (left > 0 && 2 * live_pts < tabled_points_) {
+        compact_ = true;
+        tables_dirty_ = true;
+      }
+    }
     if (left == 0) break;
     const int64_t n = std::min<int64_t>(ref ? opt.refine_period : opt.check_every, max_sweeps - m);
     if (ref) step_refine(n);
@@ -878,6 +901,10 @@ void Workset::solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>&
   std::fill(ctl.begin(), ctl.end(), 8);
   for (int k : slots) ctl[k] = ref ? (1 | 4) : 1;
   apply_slot_ctl(ctl);
+  if (compact_) {  // every solve back in the tables (field reads use them)
+    compact_ = false;
+    rebuild_tables();
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -998,6 +1025,7 @@ void Workset::autotune() {
   if (!ref) cands.push_back(Cand{32, 0, 1});
   const int sweeps = 8;
   {
+    bool first = true;
     for (const Cand& cd : cands) {
       const int64_t r = cd.rows, sc = cd.sched;
       opt_rows = r;
@@ -1008,13 +1036,20 @@ void Workset::autotune() {
         if (ref) refine_inner(sweeps);
         else sweeps_f64(sweeps, false);
       };
-      run();  // warm-up
-      cuda_check(cudaEventRecord(a, stream_), "event");
-      run();
-      cuda_check(cudaEventRecord(b, stream_), "event");
-      cuda_check(cudaEventSynchronize(b), "event");
-      float ms = 0.f;
-      cuda_check(cudaEventElapsedTime(&ms, a, b), "event");
+      // warm-up (the first candidate longer, so that clocks and caches have
+      // settled before anything is timed), then the best of three timings
+      for (int w = 0; w < (first ? 8 : 1); ++w) run();
+      first = false;
+      float ms = 1e30f;
+      for (int rep = 0; rep < 3; ++rep) {
+        cuda_check(cudaEventRecord(a, stream_), "event");
+        run();
+        cuda_check(cudaEventRecord(b, stream_), "event");
+        cuda_check(cudaEventSynchronize(b), "event");
+        float t = 0.f;
+        cuda_check(cudaEventElapsedTime(&t, a, b), "event");
+        ms = std::min(ms, t);
+      }
       if (ms < best) {
         best = ms;
         best_rows = r;

@@ -112,7 +112,7 @@ struct Options {
   int64_t poison_wait = 0;   // test hook: every dependency wait of the persistent kernel runs out
   int64_t autotune = 0;      // 1: pick rows/schedule by timing before the first solve
   int64_t emu_adds = 0;      // FP64 sweep: additions per warp step done on the integer pipe (0, 2, 3)
-  int64_t tma = 0;           // 2D inner sweeps: stage lines in shared memory with bulk async copies
+  int64_t tma = 0;           // inner sweeps (2D and 3D): stage lines in shared memory with bulk async copies
   int64_t march = 1;         // FP64 sweeps without a residual: one warp computes all segments of a line range
   int64_t outer_split = 1;   // 3D outer step as x += e over the layout, then the residual pass
 };
@@ -227,6 +227,11 @@ class Workset {
   WorkItem* d_wlo_ = nullptr;
   WorkItem* d_wm_ = nullptr;
   int nm_ = 0;
+  int estage_ = 0;  // staged 3D inner sweep: e elements per stage per warp
+  // solve_all: tables hold only the active solves (retired ones dropped once
+  // they are most of the tabled points); restored before solve_all returns
+  bool compact_ = false;
+  int64_t tabled_points_ = 0;
   CtaTask* d_t64_ = nullptr;
   CtaTask* d_tlo_ = nullptr;
   uint32_t* d_done_ = nullptr;

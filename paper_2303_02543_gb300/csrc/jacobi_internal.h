@@ -168,6 +168,11 @@ int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, 
 // 2D inner sweep (not the first of a step) with rows staged in shared memory
 // by bulk asynchronous copies; a timed-out wait sets ctl->status bit 1.
 int launch_sweep_low_tma(const Tables& t, int epar, bool push, int low, bool r_bf16, void* stream);
+// 3D inner sweep (not the first of a step) with the rows of e and r a warp
+// needs staged in shared memory by 16-byte asynchronous copies; estage =
+// elements of e per stage per warp (the largest (R + 2) * L * V over the
+// workset's blocks).
+int launch_sweep_low_stage3(const Tables& t, int epar, bool push, int low, bool r_bf16, int estage, void* stream);
 int launch_refine_outer(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream);
 // The outer step in two passes: x[phase^1] = x[phase] + e over every element
 // of the layout (ghosts included: e's ghosts hold the neighbours' values and

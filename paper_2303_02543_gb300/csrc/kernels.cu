@@ -1220,6 +1220,232 @@ k_low_tma(const WorkItem* __restrict__ items, int nitems, const BlockDev* __rest
 }
 
 // ---------------------------------------------------------------------------
+// 3D inner sweep with shared-memory staging (non-first sweeps).
+//
+// Same items and arithmetic as low_item in 3D: a warp computes R = 32 / L
+// adjacent block rows y0 .. y0+R-1 (L lanes per row) of one segment, marching
+// along z.  For every z-line the warp needs, its lanes copy into a ring of
+// kStages3 stages in shared memory, by 16-byte asynchronous copies
+// (cp.async, one commit group per line): e of rows y0-1 .. y0+R (its own rows
+// and the rows above and below) and r of its own rows.  The march keeps e of
+// lines z-1 and z of its own points in registers; e of line z+1 and of rows
+// y-1 and y+1, and r, come from shared memory, so each row of e crosses from
+// L2 once per warp instead of three times, and the copies in flight (up to
+// kStages3 - 1 lines ahead) cost no registers.  Edge scalars (the x-ghost
+// columns, the neighbouring segment's points) are plain loads one line ahead.
+
+constexpr int kStages3 = 5;
+
+// Shared-memory bytes of one warp's ring (NS stages of e and r), rounded up to
+// 128 bytes so every warp's copies land 16-byte aligned.
+template <typename TE, typename TR>
+__host__ __device__ constexpr int stage3_warp_bytes(int estage) {
+  return (kStages3 * (estage * (int)sizeof(TE) + 32 * low_vpl<TE>() * (int)sizeof(TR)) + 127) / 128 * 128;
+}
+
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <bool PUSH, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads, 2)
+k_low_stage3(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
+             const SolveDev* __restrict__ solves, int epar, int estage) {
+  constexpr int V = low_vpl<TE>();
+  constexpr int NS = kStages3;
+  constexpr int RST = 32 * V;  // r elements per stage: R rows of L * V points
+  extern __shared__ __align__(128) unsigned char st3_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int w = blockIdx.x * kWarps + warp;
+  if (w >= nitems) return;  // whole warp; warps never synchronise with each other here
+  const WorkItem it = items[w];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  if (!S->active) return;
+  unsigned char* wb = st3_smem + warp * stage3_warp_bytes<TE, TR>(estage);
+  TE* se = reinterpret_cast<TE*>(wb);                                  // NS stages of (R+2) rows of e
+  TR* sr = reinterpret_cast<TR*>(wb + NS * estage * (int)sizeof(TE));  // NS stages of R rows of r
+  const TE* __restrict__ es = reinterpret_cast<const TE*>(S->e[epar ^ 1]);
+  TE* __restrict__ ed = reinterpret_cast<TE*>(S->e[epar]);
+  const TR* __restrict__ rr = reinterpret_cast<const TR*>(S->r);
+
+  const int lgL = low_lanes_log2(B.bx, V);
+  const int L = 1 << lgL, R = 32 >> lgL;
+  const int SEGW = L * V;
+  const int rg = lane >> lgL, l = lane & (L - 1);
+  const int y = it.y0 + rg;
+  const bool row_ok = y < B.by;
+  const int bx = B.bx;
+  const int xs = it.seg * SEGW;
+  const int x = xs + V * l;
+  const int nvalid = row_ok ? bx - x : 0;
+  const bool any = nvalid > 0;
+  const int64_t gW = B.xoff;
+  const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
+  const Geo<3> G(B, row_ok ? y : B.by - 1);
+  PushTargets T;
+  if constexpr (PUSH) push_targets<3>(T, B, blocks, row_ok ? y : B.by - 1);
+  // rows of e staged per line: y0-1 .. ylast+1 (ylast the warp's last row in
+  // the block; row by is the ghost row); elements per row: cnt, a multiple of
+  // 16 bytes inside the row pitch
+  const int ylast = min(it.y0 + R - 1, B.by - 1);
+  const int nrows_e = ylast - it.y0 + 3, nrows_r = ylast - it.y0 + 1;
+  const int cnt = min(SEGW, B.pitch - xs);
+  const int ecpr = cnt * (int)sizeof(TE) / 16, rcpr = cnt * (int)sizeof(TR) / 16;  // 16-byte chunks per row
+  const int m0 = it.z0, mend = m0 + it.n;
+  const int L0 = m0 - 1, L1 = mend;  // e lines L0..L1; r lines m0..mend-1
+  auto row_off = [&](int yy, int m) {  // element offset of (x = xs, row yy, line m)
+    return B.off + (int64_t)(m + 1) * B.plane + (int64_t)(yy + 1) * B.pitch + xs;
+  };
+  // every lane: copy its share of line Ln into stage (Ln - L0) % NS, then
+  // commit one group (empty past the last line, so the group count per
+  // step stays constant)
+  auto issue = [&](int Ln) {
+    if (Ln <= L1) {
+      const int st = (Ln - L0) % NS;
+      for (int c = lane; c < nrows_e * ecpr; c += 32) {
+        const int j = c / ecpr, k = c - j * ecpr;
+        cp_async16(reinterpret_cast<unsigned char*>(se + st * estage + j * SEGW) + 16 * k,
+                   reinterpret_cast<const unsigned char*>(es + row_off(it.y0 - 1 + j, Ln)) + 16 * k);
+      }
+      if (Ln >= m0 && Ln < mend)
+        for (int c = lane; c < nrows_r * rcpr; c += 32) {
+          const int j = c / rcpr, k = c - j * rcpr;
+          cp_async16(reinterpret_cast<unsigned char*>(sr + st * RST + j * SEGW) + 16 * k,
+                     reinterpret_cast<const unsigned char*>(rr + row_off(it.y0 + j, Ln)) + 16 * k);
+        }
+    }
+    cp_async_commit();
+  };
+  auto ld_e = [&](int st, int j, float (&o)[V]) {  // this lane's V values of staged row j
+    const TE* q = se + st * estage + j * SEGW + V * l;
+    if constexpr (sizeof(TE) == 4) {
+      const float4 a = *reinterpret_cast<const float4*>(q);
+      o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+    } else {
+      const uint4 u = *reinterpret_cast<const uint4*>(q);
+      const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        o[2 * k] = __uint_as_float(wv[k] << 16);
+        o[2 * k + 1] = __uint_as_float(wv[k] & 0xFFFF0000u);
+      }
+    }
+  };
+  auto ld_r = [&](int st, float (&o)[V]) {
+    const TR* q = sr + st * RST + rg * SEGW + V * l;
+    if constexpr (sizeof(TR) == 4) {
+      const float4 a = *reinterpret_cast<const float4*>(q);
+      o[0] = a.x; o[1] = a.y; o[2] = a.z; o[3] = a.w;
+      if constexpr (V == 8) {
+        const float4 b = *reinterpret_cast<const float4*>(q + 4);
+        o[4] = b.x; o[5] = b.y; o[6] = b.z; o[7] = b.w;
+      }
+    } else {
+      const uint4 u = *reinterpret_cast<const uint4*>(q);
+      const uint32_t wv[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        o[2 * k] = __uint_as_float(wv[k] << 16);
+        o[2 * k + 1] = __uint_as_float(wv[k] & 0xFFFF0000u);
+      }
+    }
+  };
+  // edge scalars of line m (west of point 0, east of point V-1, the east
+  // ghost of the block's last point), fetched one line ahead
+  auto edges = [&](int m, float& wv, float& ev, float& ge) {
+    const int64_t lc = G.line(m);
+    const int col = G.col(m);
+    wv = ev = ge = 0.f;
+    if (any) {
+      if (l == 0) wv = xs > 0 ? ldf<false>(es + lc + xs - 1) : ldf<false>(es + gW + col);
+      if (l == L - 1 && x + V < bx) ev = ldf<false>(es + lc + x + V);
+      if (nvalid <= V) ge = ldf<false>(es + gE + col);
+    }
+  };
+  for (int i = 0; i < NS; ++i) issue(L0 + i);
+  cp_async_wait<NS - 2>();  // lines L0 and L0 + 1 = m0 have landed
+  __syncwarp();
+  float p[V], c[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) p[k] = c[k] = 0.f;
+  if (any) {
+    ld_e(0, rg + 1, p);
+    ld_e(1 % NS, rg + 1, c);
+  }
+  float wv, ev, ge;
+  edges(m0, wv, ev, ge);
+  __syncwarp();   // line L0's stage is free once every lane has read p
+  issue(L0 + NS);
+  for (int m = m0; m < mend; ++m) {
+    const int64_t lc = G.line(m);
+    const int col = G.col(m);
+    float wn = 0.f, en = 0.f, gn = 0.f;
+    if (m + 1 < mend) edges(m + 1, wn, en, gn);
+    cp_async_wait<NS - 2>();  // line m + 1 (the oldest pending group) has landed
+    __syncwarp();
+    const int stc = (m - L0) % NS, stn = (m + 1 - L0) % NS;
+    float n[V], sa[V], sb[V], rv[V], o[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) n[k] = sa[k] = sb[k] = rv[k] = 0.f;
+    if (any) {
+      ld_e(stn, rg + 1, n);
+      ld_e(stc, rg, sa);
+      ld_e(stc, rg + 2, sb);
+      ld_r(stc, rv);
+    }
+    float wl = __shfl_up_sync(FULL_MASK, c[V - 1], 1, L);
+    if (l == 0) wl = wv;
+    float el = __shfl_down_sync(FULL_MASK, c[0], 1, L);
+    if (l == L - 1 && x + V < bx) el = ev;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const float west = k == 0 ? wl : c[k - 1];
+      float east = k == V - 1 ? el : c[k + 1];
+      if (k + 1 == nvalid) east = ge;  // the block's last point takes the ghost
+      float t = __fadd_rn(__fadd_rn(west, p[k]), __fadd_rn(east, n[k]));
+      t = __fadd_rn(t, __fadd_rn(sa[k], sb[k]));
+      t = __fadd_rn(t, rv[k]);
+      o[k] = jdivf<3>(t);
+    }
+    // line m's stage is free once every lane has read it: refill it
+    __syncwarp();
+    issue(m + NS);
+    if (any) {
+      stv<V>(ed + lc + x, o, nvalid);
+      if constexpr (PUSH) {
+        if (m == 0 && T.lo_line >= 0) stv<V>(ed + T.lo_line + x, o, nvalid);
+        if (m == G.extent - 1 && T.hi_line >= 0) stv<V>(ed + T.hi_line + x, o, nvalid);
+        if (T.lo_side >= 0) stv<V>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
+        if (T.hi_side >= 0) stv<V>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
+        if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o[0]);
+        if (nvalid <= V && T.e_col >= 0) {
+          float last = o[0];
+#pragma unroll
+          for (int k = 1; k < V; ++k)
+            if (k == nvalid - 1) last = o[k];
+          ed[T.e_col + col] = from_f<TE>(last);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      p[k] = c[k];
+      c[k] = n[k];
+    }
+    wv = wn;
+    ev = en;
+    ge = gn;
+  }
+  cp_async_wait<0>();  // no copy may still target this warp's shared memory on exit
+}
+
+// ---------------------------------------------------------------------------
 // Persistent block scheduler (section 3.1.4's push/pop scheduler and the
 // implicit dependencies of section 3.1.2, moved onto the device).  A task is
 // one CTA's worth of warp items of one block; (sweep j, task t) pairs are
@@ -1796,6 +2022,25 @@ static int low_tma_typed(const Tables& t, int epar, bool push, cudaStream_t s) {
   k<<<grid_of(t.nlo, kWarps), kThreads, smem, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar, &t.ctl->status,
                                                    t.spin_limit);
   return (int)cudaGetLastError();
+}
+
+template <typename TE, typename TR>
+static int low_stage3_typed(const Tables& t, int epar, bool push, int estage, cudaStream_t s) {
+  const int smem = kWarps * stage3_warp_bytes<TE, TR>(estage);
+  auto k = push ? k_low_stage3<true, TE, TR> : k_low_stage3<false, TE, TR>;
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return (int)e;
+  k<<<grid_of(t.nlo, kWarps), kThreads, smem, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar, estage);
+  return (int)cudaGetLastError();
+}
+
+int launch_sweep_low_stage3(const Tables& t, int epar, bool push, int low, bool r_bf16, int estage, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.nlo == 0) return 0;
+  if (t.ndim != 3 || estage <= 0) return (int)cudaErrorInvalidValue;
+  if (low == kLowF32) return low_stage3_typed<float, float>(t, epar, push, estage, s);
+  if (r_bf16) return low_stage3_typed<__nv_bfloat16, __nv_bfloat16>(t, epar, push, estage, s);
+  return low_stage3_typed<__nv_bfloat16, float>(t, epar, push, estage, s);
 }
 
 int launch_sweep_low_tma(const Tables& t, int epar, bool push, int low, bool r_bf16, void* stream) {

@@ -349,7 +349,11 @@ def test_residual_decomposition_independent_3d():
 @pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False),
                                            ("bf16r16_refine", True, True)])
 @pytest.mark.parametrize("dims,block", [((60, 45), (32, 16)), ((300, 70), (130, 33)), ((513, 9), (513, 9)),
-                                        ((7, 200), (7, 64))])
+                                        ((7, 200), (7, 64)),
+                                        # 3D: several rows per warp with idle rows, remainder
+                                        # blocks, rows two warp segments wide, one-line items
+                                        ((40, 33, 20), (32, 11, 20)), ((70, 9, 8), (64, 5, 4)),
+                                        ((300, 4, 5), (300, 4, 5)), ((5, 7, 3), (5, 7, 1))])
 def test_staged_inner_sweeps_match_oracle(dtype, e16, r16, dims, block):
     """Inner sweeps with lines staged in shared memory by bulk copies give the
     same bits as the register path and the oracle's emulation."""
