@@ -77,6 +77,7 @@ def parse():
     ap.add_argument("--tma", type=int, default=-1, help="2D inner sweeps staged by bulk async copies (0/1)")
     ap.add_argument("--march", type=int, default=-1, help="2D FP64 sweeps over march items (0/1)")
     ap.add_argument("--outer-split", type=int, default=-1, help="3D outer step in two passes (0/1)")
+    ap.add_argument("--rows-low", type=int, default=0, help="lines per low-precision work item (0: library default)")
     ap.add_argument("--ref-sweeps", type=int, default=0,
                     help="tts3d_512: sweep count of a refinement solve measured earlier, for the FP64 extrapolation "
                          "when only f64 runs")
@@ -255,6 +256,8 @@ def time_form(p, form, sweeps, args, world, stream, sampler=None):
         opts["tma"] = args.tma
     if form != "f64" and args.outer_split >= 0:
         opts["outer_split"] = args.outer_split
+    if form != "f64" and args.rows_low > 0:
+        opts["rows_low"] = args.rows_low
     s = J.Solver(p.dims, p.block, dtype=form, faces=p.faces, source=p.source, x0=p.x0,
                  check_every=CHECK_EVERY, refine_period=CHECK_EVERY, profile=1, **opts)
 

@@ -889,6 +889,12 @@ void Workset::solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>&
       if (left > 0 && 2 * live_pts < tabled_points_) {
         compact_ = true;
         tables_dirty_ = true;
+        // the work shape tuned for the whole batch may leave the GPU idle
+        // once only the largest grids remain: tune again for the active ones
+        if (opt.autotune) {
+          tuned_ = false;
+          autotune();
+        }
       }
     }
     if (left == 0) break;
@@ -921,7 +927,7 @@ static std::string tune_key(const Workset& w, const std::vector<SolveHost*>& sol
   cudaGetDeviceProperties(&prop, dev);
   int64_t pts = 0, nb = 0, bx = 0, by = 0, bz = 0;
   for (auto* s : solves)
-    if (s) {
+    if (s && s->active) {
       pts += s->points();
       nb += (int64_t)s->blocks.size();
       bx = s->spec.blk[0];

@@ -175,3 +175,25 @@ def test_split_outer_step_3d_bit_exact(dtype, e16, r16, graph):
                                                  e_bf16=e16, r_bf16=r16)
         assert fields[1][1][i] == sw_o
         assert np.array_equal(fields[1][0][i], x_o)
+
+
+@pytest.mark.parametrize("dtype", ["f32_refine", "f64"])
+def test_batch_retune_after_compaction_keeps_results(dtype, tmp_path, monkeypatch):
+    """With the autotuner on, a batch whose solves retire at different times is
+    re-tuned for the remaining ones once they are a minority of the points;
+    every result is still the one the solve gives alone."""
+    monkeypatch.setenv("JACOBI_TUNE_CACHE", str(tmp_path / "tune.jsonl"))
+    probs = uneven_problems(6, 83, 0.06)
+    tol = 1e-8 if dtype != "f64" else 1e-6
+    with J.Batch(probs, dtype=dtype, refine_period=20, check_every=20, autotune=1, graph=1) as b:
+        st, res = b.solve(tol, 10 ** 6)
+        mix = [b.field(i) for i in range(len(probs))]
+    assert st == J.OK
+    for i, p in enumerate(probs):
+        with J.Batch([p], dtype=dtype, refine_period=20, check_every=20) as b1:
+            st1, r1 = b1.solve(tol, 10 ** 6)
+            alone = b1.field(0)
+        assert st1 == J.OK and r1[0][1] == res[i][1]
+        assert np.array_equal(alone, mix[i])
+    lines = (tmp_path / "tune.jsonl").read_text().splitlines()
+    assert len(lines) >= 2  # the first tuning and at least one re-tuning
