@@ -84,6 +84,7 @@ def parse():
     ap.add_argument("--march", type=int, default=-1, help="2D FP64 sweeps over march items (0/1)")
     ap.add_argument("--outer-split", type=int, default=-1, help="3D outer step in two passes (0/1)")
     ap.add_argument("--rows-low", type=int, default=0, help="lines per low-precision work item (0: library default)")
+    ap.add_argument("--server-opts", default="", help="serving: server options as key=value,key=value")
     ap.add_argument("--ref-sweeps", type=int, default=0,
                     help="tts3d_512: sweep count of a refinement solve measured earlier, for the FP64 extrapolation "
                          "when only f64 runs")
@@ -537,7 +538,11 @@ def run_serving(args, rank, world, local):
     torch.cuda.set_device(local)
     stream = inputs.serving_stream(rate=args.rate, window_s=args.window, lo2=128, hi2=args.cap2d, lo3=32,
                                    hi3=args.cap3d)
-    srv = J.Server("f32_refine", budget_bytes=64 << 30, max_slots=256, refine_period=20)
+    sopts = dict(refine_period=20)
+    for kv in filter(None, args.server_opts.split(",")):
+        k, v = kv.split("=")
+        sopts[k.strip()] = int(v)
+    srv = J.Server("f32_refine", budget_bytes=64 << 30, max_slots=256, **sopts)
     t0 = time.perf_counter()
     tickets = []
     for a in stream:
@@ -569,7 +574,8 @@ def run_serving(args, rank, world, local):
                           "p50_ms": pct(0.5), "p99_ms": pct(0.99), "glups": lups / wall / 1e9,
                           "steps": stats["steps"], "higher_is_better": False,
                           "config": {"cap2d": args.cap2d, "cap3d": args.cap3d, "dtype": "f32_refine",
-                                     "refine_period": 20, "note": "sizes capped (full 4096^2 solves take ~1 h each)"},
+                                     "server_options": sopts,
+                                     "note": "sizes capped (full 4096^2 solves take ~1 h each)"},
                           "data": "synthetic"}), flush=True)
 
 

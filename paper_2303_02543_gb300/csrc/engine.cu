@@ -845,6 +845,20 @@ void Workset::chunk_f64(int64_t n) {
 void Workset::solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>& res) {
   if (tables_dirty_) rebuild_tables();
   if (opt.autotune && !tuned_) autotune();
+  // however the loop ends (also by an exception), tables compacted to the
+  // active solves are marked for a full rebuild, and a work shape re-tuned
+  // for the last solves is not kept for the next call
+  struct CompactGuard {
+    Workset* w;
+    bool retuned = false;
+    ~CompactGuard() {
+      if (w->compact_) {
+        w->compact_ = false;
+        w->tables_dirty_ = true;
+      }
+      if (retuned) w->tuned_ = false;
+    }
+  } guard{this};
   res.assign(capacity_, SlotResult());
   std::vector<int> slots;
   for (int k = 0; k < capacity_; ++k)
@@ -894,6 +908,7 @@ void Workset::solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>&
         if (opt.autotune) {
           tuned_ = false;
           autotune();
+          guard.retuned = true;
         }
       }
     }
@@ -907,10 +922,6 @@ void Workset::solve_all(double tol, int64_t max_sweeps, std::vector<SlotResult>&
   std::fill(ctl.begin(), ctl.end(), 8);
   for (int k : slots) ctl[k] = ref ? (1 | 4) : 1;
   apply_slot_ctl(ctl);
-  if (compact_) {  // every solve back in the tables (field reads use them)
-    compact_ = false;
-    rebuild_tables();
-  }
 }
 
 // ---------------------------------------------------------------------------

@@ -354,7 +354,11 @@ jacobi_status jacobi_server_create(jacobi_server_t* out, int dtype, int64_t hbm_
   srv->dtype = dtype;
   srv->max_slots = max_slots;
   srv->stream = (cudaStream_t)cuda_stream;
-  srv->opt.schedule = 1;
+  // one launch per sweep, each refinement step replayed from a CUDA graph:
+  // on a stream of small solves this steps faster than the persistent
+  // scheduler (whose per-block waits dominate small grids)
+  srv->opt.schedule = 0;
+  srv->opt.graph = 1;
   memset(&srv->stats, 0, sizeof(srv->stats));
   cudaGetDevice(&srv->device);
   if (!srv->arena.init((size_t)hbm_budget_bytes, current_alloc_hooks(), srv->stream)) {
