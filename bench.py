@@ -85,6 +85,7 @@ def parse():
     ap.add_argument("--outer-split", type=int, default=-1, help="3D outer step in two passes (0/1)")
     ap.add_argument("--rows-low", type=int, default=0, help="lines per low-precision work item (0: library default)")
     ap.add_argument("--server-opts", default="", help="serving: server options as key=value,key=value")
+    ap.add_argument("--block", default="", help="override the workload's block shape, e.g. 512,64,64")
     ap.add_argument("--ref-sweeps", type=int, default=0,
                     help="tts3d_512: sweep count of a refinement solve measured earlier, for the FP64 extrapolation "
                          "when only f64 runs")
@@ -337,6 +338,9 @@ def run_ours(args, rank, world, local):
     torch.cuda.set_device(local)
     stream = torch.cuda.current_stream()
     p, desc, sweeps = make_workload(args.workload)
+    if args.block:
+        p.block = tuple(int(v) for v in args.block.split(","))
+        desc += f" (blocks overridden to {'x'.join(map(str, p.block))})"
     if args.sweeps > 0:
         sweeps = args.sweeps
     hbm_peak, peak_kind = measured_peaks()

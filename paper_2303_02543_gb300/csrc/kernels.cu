@@ -887,87 +887,87 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
       }
       cur = nx;
     }
-    return;
-  }
-  for (int m = m0; m < mend; ++m) {
-    const int64_t lc = G.line(m);
-    const int col = G.col(m);
-    float rv[V], o[V];
+  } else {
+    for (int m = m0; m < mend; ++m) {
+      const int64_t lc = G.line(m);
+      const int col = G.col(m);
+      float rv[V], o[V];
 #pragma unroll
-    for (int k = 0; k < V; ++k) rv[k] = 0.f;
-    if (any) ldv<false, V>(rr + lc + x, rv);  // r is read-only during every sweep
-    float n[V];
+      for (int k = 0; k < V; ++k) rv[k] = 0.f;
+      if (any) ldv<false, V>(rr + lc + x, rv);  // r is read-only during every sweep
+      float n[V];
 #pragma unroll
-    for (int k = 0; k < V; ++k) n[k] = 0.f;
-    if constexpr (FIRST) {
+      for (int k = 0; k < V; ++k) n[k] = 0.f;
+      if constexpr (FIRST) {
 #pragma unroll
-      for (int k = 0; k < V; ++k) o[k] = jdivf<DIM>(__fadd_rn(0.0f, rv[k]));
-    } else {
-      if (any) ldv<COH, V>(es + G.line(m + 1) + x, n);
-      float sa[V], sb[V];
-#pragma unroll
-      for (int k = 0; k < V; ++k) sa[k] = sb[k] = 0.f;
-      if constexpr (DIM == 3) {
-        if (any) {
-          ldv<COH, V>(es + lc - G.side + x, sa);
-          ldv<COH, V>(es + lc + G.side + x, sb);
-        }
-      }
-      // west of point 0, east of point V-1 (in 3D the shuffles stay inside
-      // the row's L lanes; the 2D forms are written apart, as the compiler
-      // schedules the plain ones measurably better)
-      float wv, ev;
-      if constexpr (DIM == 2) {
-        wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
-        if (lane == 0) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
-        ev = __shfl_down_sync(FULL_MASK, c[0], 1);
-        if (lane == 31 && x + V < bx) ev = ldf<COH>(es + lc + x + V);
+        for (int k = 0; k < V; ++k) o[k] = jdivf<DIM>(__fadd_rn(0.0f, rv[k]));
       } else {
-        wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1, L);
-        if (l == 0 && any) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
-        ev = __shfl_down_sync(FULL_MASK, c[0], 1, L);
-        if (l == L - 1 && any && x + V < bx) ev = ldf<COH>(es + lc + x + V);
-      }
-      float ge = 0.f;
-      if (any && nvalid <= V) ge = ldf<COH>(es + gE + col);
+        if (any) ldv<COH, V>(es + G.line(m + 1) + x, n);
+        float sa[V], sb[V];
 #pragma unroll
-      for (int k = 0; k < V; ++k) {
-        const float west = k == 0 ? wv : c[k - 1];
-        float east = k == V - 1 ? ev : c[k + 1];
-        if (k + 1 == nvalid) east = ge;  // the block's last point takes the ghost
-        float t = __fadd_rn(__fadd_rn(west, p[k]), __fadd_rn(east, n[k]));
-        if constexpr (DIM == 3) t = __fadd_rn(t, __fadd_rn(sa[k], sb[k]));
-        t = __fadd_rn(t, rv[k]);
-        o[k] = jdivf<DIM>(t);
-      }
-    }
-    if (any) {
-      stv<V>(ed + lc + x, o, nvalid);
-      if constexpr (PUSH) {
-        if (m == 0 && T.lo_line >= 0) stv<V>(ed + T.lo_line + x, o, nvalid);
-        if (m == G.extent - 1 && T.hi_line >= 0) stv<V>(ed + T.hi_line + x, o, nvalid);
+        for (int k = 0; k < V; ++k) sa[k] = sb[k] = 0.f;
         if constexpr (DIM == 3) {
-          if (T.lo_side >= 0) stv<V>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
-          if (T.hi_side >= 0) stv<V>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
+          if (any) {
+            ldv<COH, V>(es + lc - G.side + x, sa);
+            ldv<COH, V>(es + lc + G.side + x, sb);
+          }
         }
-        if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o[0]);
-        if (nvalid <= V && T.e_col >= 0) {
-          float last = o[0];
+        // west of point 0, east of point V-1 (in 3D the shuffles stay inside
+        // the row's L lanes; the 2D forms are written apart, as the compiler
+        // schedules the plain ones measurably better)
+        float wv, ev;
+        if constexpr (DIM == 2) {
+          wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1);
+          if (lane == 0) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
+          ev = __shfl_down_sync(FULL_MASK, c[0], 1);
+          if (lane == 31 && x + V < bx) ev = ldf<COH>(es + lc + x + V);
+        } else {
+          wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1, L);
+          if (l == 0 && any) wv = xs > 0 ? ldf<COH>(es + lc + xs - 1) : ldf<COH>(es + gW + col);
+          ev = __shfl_down_sync(FULL_MASK, c[0], 1, L);
+          if (l == L - 1 && any && x + V < bx) ev = ldf<COH>(es + lc + x + V);
+        }
+        float ge = 0.f;
+        if (any && nvalid <= V) ge = ldf<COH>(es + gE + col);
 #pragma unroll
-          for (int k = 1; k < V; ++k)
-            if (k == nvalid - 1) last = o[k];
-          ed[T.e_col + col] = from_f<TE>(last);
+        for (int k = 0; k < V; ++k) {
+          const float west = k == 0 ? wv : c[k - 1];
+          float east = k == V - 1 ? ev : c[k + 1];
+          if (k + 1 == nvalid) east = ge;  // the block's last point takes the ghost
+          float t = __fadd_rn(__fadd_rn(west, p[k]), __fadd_rn(east, n[k]));
+          if constexpr (DIM == 3) t = __fadd_rn(t, __fadd_rn(sa[k], sb[k]));
+          t = __fadd_rn(t, rv[k]);
+          o[k] = jdivf<DIM>(t);
         }
       }
-    }
-    if constexpr (!FIRST) {
+      if (any) {
+        stv<V>(ed + lc + x, o, nvalid);
+        if constexpr (PUSH) {
+          if (m == 0 && T.lo_line >= 0) stv<V>(ed + T.lo_line + x, o, nvalid);
+          if (m == G.extent - 1 && T.hi_line >= 0) stv<V>(ed + T.hi_line + x, o, nvalid);
+          if constexpr (DIM == 3) {
+            if (T.lo_side >= 0) stv<V>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
+            if (T.hi_side >= 0) stv<V>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
+          }
+          if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o[0]);
+          if (nvalid <= V && T.e_col >= 0) {
+            float last = o[0];
 #pragma unroll
-      for (int k = 0; k < V; ++k) {
-        p[k] = c[k];
-        c[k] = n[k];
+            for (int k = 1; k < V; ++k)
+              if (k == nvalid - 1) last = o[k];
+            ed[T.e_col + col] = from_f<TE>(last);
+          }
+        }
       }
-    }
+      if constexpr (!FIRST) {
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+          p[k] = c[k];
+          c[k] = n[k];
+        }
+      }
   }
+}
 }
 
 // Launch bounds measured per form: bfloat16 in 2D runs best held to 4 CTAs
