@@ -146,7 +146,8 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
  *                    1 = separate pack and unpack kernels after every sweep
  *                    (section 4.3's pack / transfer / unpack steps)
  *   "rows_f64"       lines per warp work item of the FP64 kernels (default 32)
- *   "rows_low"       lines per warp work item of the low-precision kernels (default 32)
+ *   "rows_low"       lines per warp work item of the low-precision kernels; 0
+ *                    (default) chooses 16 (float) or 8 (bfloat16) in 2D, 32 in 3D
  *   "schedule"       0 = one launch per sweep (default); 1 = persistent block
  *                    scheduler: one launch runs many sweeps, blocks wait for
  *                    their neighbours' previous sweep, never for a global

@@ -258,7 +258,8 @@ jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value) {
   int64_t* p = option_slot(ws.opt, key);
   require(p != nullptr, std::string("unknown option ") + (key ? key : "(null)"));
   const std::string k(key);
-  if (k == "check_every" || k == "rows_f64" || k == "rows_low") require(value >= 1, k + " must be >= 1");
+  if (k == "check_every" || k == "rows_f64") require(value >= 1, k + " must be >= 1");
+  if (k == "rows_low") require(value >= 0, "rows_low must be >= 0 (0: automatic)");
   if (k == "refine_period") require(value >= 1 && value <= 4096, "refine_period must be in [1, 4096]");
   if (k == "halo" || k == "profile" || k == "schedule" || k == "graph" || k == "poison_wait" || k == "autotune" ||
       k == "tma" || k == "march" || k == "outer_split")

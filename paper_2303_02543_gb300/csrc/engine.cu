@@ -318,7 +318,10 @@ void Workset::rebuild_tables() {
   // FP64 items hold whole residual groups (a group is reduced by one warp)
   const int r64 = (int)std::min<int64_t>((std::max<int64_t>(opt.rows_f64, 1) + kResGroup - 1) / kResGroup * kResGroup,
                                          32760);
-  const int rlo = (int)std::min<int64_t>(std::max<int64_t>(opt.rows_low, 1), 32767);
+  // rows_low = 0: lines per low-precision item by form (measured at 8192^2 /
+  // 512^3): 2D 16 (float) or 8 (bfloat16), 3D 32
+  const int64_t rows_low_auto = ndim_ == 2 ? (low() == kLowBF16 ? 8 : 16) : 32;
+  const int rlo = (int)std::min<int64_t>(std::max<int64_t>(opt.rows_low > 0 ? opt.rows_low : rows_low_auto, 1), 32767);
   // 2D FP64 march items: as many as the march kernel keeps resident (one
   // wave), each at least 8 and at most kMarchLines lines long, the lines of a
   // block split evenly

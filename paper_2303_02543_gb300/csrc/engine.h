@@ -104,7 +104,7 @@ struct Options {
   int64_t refine_period = 20;
   int64_t halo = 0;          // 0 fused, 1 standalone pack/unpack
   int64_t rows_f64 = 32;
-  int64_t rows_low = 32;
+  int64_t rows_low = 0;      // 0: chosen by dimensionality and type (see rebuild_tables)
   int64_t profile = 0;
   int64_t schedule = 0;      // 0 one launch per sweep, 1 persistent block scheduler
   int64_t graph = 0;         // 1: replay each solve step from a captured CUDA graph
