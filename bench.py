@@ -84,6 +84,7 @@ def parse():
     ap.add_argument("--march", type=int, default=-1, help="2D FP64 sweeps over march items (0/1)")
     ap.add_argument("--outer-split", type=int, default=-1, help="3D outer step in two passes (0/1)")
     ap.add_argument("--rows-low", type=int, default=0, help="lines per low-precision work item (0: library default)")
+    ap.add_argument("--rows-f64", type=int, default=0, help="lines per FP64 work item (0: library default)")
     ap.add_argument("--server-opts", default="", help="serving: server options as key=value,key=value")
     ap.add_argument("--block", default="", help="override the workload's block shape, e.g. 512,64,64")
     ap.add_argument("--ref-sweeps", type=int, default=0,
@@ -266,6 +267,8 @@ def time_form(p, form, sweeps, args, world, stream, sampler=None):
         opts["outer_split"] = args.outer_split
     if form != "f64" and args.rows_low > 0:
         opts["rows_low"] = args.rows_low
+    if args.rows_f64 > 0:
+        opts["rows_f64"] = args.rows_f64
     s = J.Solver(p.dims, p.block, dtype=form, faces=p.faces, source=p.source, x0=p.x0,
                  check_every=CHECK_EVERY, refine_period=refine_period_of(p), profile=1, **opts)
 

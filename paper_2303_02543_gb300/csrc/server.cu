@@ -386,7 +386,8 @@ jacobi_status jacobi_server_set_option(jacobi_server_t srv, const char* key, int
     if (value != 0 && value != 1) throw JErr{JACOBI_ERR_INVALID, k + " must be 0 or 1"};
     (k == "schedule" ? srv->opt.schedule : k == "graph" ? srv->opt.graph : srv->opt.halo) = value;
   } else if (k == "rows_low" || k == "rows_f64") {
-    if (value < 1) throw JErr{JACOBI_ERR_INVALID, k + " must be >= 1"};
+    if (value < (k == "rows_low" ? 0 : 1))
+      throw JErr{JACOBI_ERR_INVALID, k == "rows_low" ? "rows_low must be >= 0 (0: automatic)" : "rows_f64 must be >= 1"};
     (k == "rows_low" ? srv->opt.rows_low : srv->opt.rows_f64) = value;
   } else {
     throw JErr{JACOBI_ERR_INVALID, "unknown server option " + k};
