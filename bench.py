@@ -57,10 +57,10 @@ BYTES_PER_LUP = {"f64": 24.0, "f32_refine": 12.0, "bf16_refine": 8.0}
 METRIC = "Jacobi GLUP/s & % HBM roofline, mixed vs FP64 at 1e-8 resid; p99 solve ms"
 # DRAM bytes (read + write) per lattice update of the 2D FP64 sweep kernel
 # (k_f64_march), from the ncu capture summarised in
-# profiles/sweep_f64_poisson2d_4096.md (270.3 MB read + 106.3 MB written for
+# profiles/sweep_f64_poisson2d_4096.md (270.2 MB read + 106.0 MB written for
 # 16.8 M updates); traffic grows with the points, so a full launch is this
 # times its points.  Must be retaken whenever that kernel changes.
-F64_SWEEP_DRAM_BYTES_PER_LUP = (270.267648e6 + 106.273280e6) / (4096 * 4096)
+F64_SWEEP_DRAM_BYTES_PER_LUP = (270.244608e6 + 106.030592e6) / (4096 * 4096)
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -70,7 +70,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="poisson2d_8192",
                     choices=["poisson2d_8192", "poisson2d_4096", "laplace2d_256", "poisson3d_512", "poisson3d_256",
-                             "tts2d_512", "tts3d_128", "tts3d_512", "batched", "serving"])
+                             "tts2d_512", "tts3d_128", "tts3d_512", "batched", "serving", "paper3d_od"])
     ap.add_argument("--scale", type=float, default=0.25, help="batched: side scale (1.0 = the full 64..2048 recipe)")
     ap.add_argument("--rate", type=float, default=10.0, help="serving: arrivals per second")
     ap.add_argument("--window", type=float, default=20.0, help="serving: arrival window, seconds")
@@ -419,6 +419,45 @@ def run_ours(args, rank, world, local):
 
 # ---- time to tolerance, batches, serving (separate lines, not the default) ---
 
+def run_paper3d_od(args, rank, world, local):
+    """The shape of the paper's Jacobi3D runs (section 4.3: a 1024x1024x768
+    domain, a fixed number of iterations; section 4.4: over-decomposition
+    levels): FP64, 100 sweeps with the residual tested every 50, the same
+    grid cut into 1, 2, 8 and 64 blocks.  With block widths multiples of 64
+    along x and 8 along z the residual does not depend on the decomposition,
+    so every level must report the same bits."""
+    import torch
+
+    from paper_2303_02543_gb300 import inputs
+    from paper_2303_02543_gb300 import jacobi as J
+    torch.cuda.set_device(local)
+    dims = (1024, 1024, 768)
+    levels = {1: (1024, 1024, 768), 2: (1024, 1024, 384), 8: (512, 512, 384), 64: (256, 256, 192)}
+    p = inputs.make_problem(dims, levels[1], 2310, boundary="zero", source="normal", x0="zero")
+    sweeps = 100
+    out, rels = {}, {}
+    for od, blk in levels.items():
+        with J.Solver(p.dims, blk, dtype="f64", faces=p.faces, source=p.source, check_every=CHECK_EVERY) as s:
+            s.solve(1e-300, 10)  # warm-up
+            s.set_field(np.zeros(p.shape))
+            torch.cuda.synchronize()
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record()
+            st, sw, rel = s.solve(1e-300, sweeps)
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            out[od] = {"blocks": int(np.prod([-(-dims[a] // blk[a]) for a in range(3)])), "block": list(blk),
+                       "ms": ms, "glups": p.points * sweeps / (ms / 1e3) / 1e9, "rel_after": rel}
+            rels[od] = rel
+    if rank == 0:
+        print(json.dumps({"metric": "Jacobi3D (paper shape) FP64 GLUP/s by over-decomposition level",
+                          "workload": "paper3d_od", "grid": list(dims), "sweeps": sweeps,
+                          "check_every": CHECK_EVERY, "od": out,
+                          "residual_identical_across_levels": len(set(rels.values())) == 1,
+                          "higher_is_better": True, "data": "synthetic"}), flush=True)
+
+
 def run_tts(args, rank, world, local):
     """Time to relative residual 1e-8: plain FP64 against FP32- and
     BF16-inner refinement on the same grid and GPU (each a real solve)."""
@@ -595,6 +634,8 @@ def main():
         run_tts(args, rank, world, local)
     elif args.workload == "batched":
         run_batched(args, rank, world, local)
+    elif args.workload == "paper3d_od":
+        run_paper3d_od(args, rank, world, local)
     elif args.workload == "serving":
         run_serving(args, rank, world, local)
     else:
