@@ -2,9 +2,9 @@
  * Jacobi oracle -- TEST INFRASTRUCTURE ONLY.
  *
  * A plain, slow, obviously-correct FP64 CPU implementation of the Jacobi
- * relaxation that the Jacobi3D proxy application runs (section 4.3: "a fixed
- * number of iterations of the Jacobi method ... in a 3D domain decomposed
- * into cuboids"), on ONE monolithic grid with a one-cell ghost ring.  The
+ * relaxation that the Jacobi3D proxy application runs (section 4.3: Jacobi
+ * iterations, a set count of them, on a 3D domain cut into cuboid pieces), on
+ * ONE monolithic grid with a one-cell ghost ring.  The
  * over-decomposition of section 4.4 changes how the work is split, not what
  * is computed, so the oracle has no blocks at all.
  *
