@@ -482,22 +482,39 @@ Tables Workset::solve_tables(const SolveHost& s) const {
   return t;
 }
 
+// Device address of a page-locked host buffer (pinned or registered), which
+// kernels can read and write directly over the host link; nullptr for any
+// other host memory, which then goes through a device staging buffer.
+static const void* locked_host_device_ptr(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 void Workset::scatter(int slot, const double* dense, int which, int on_device) {
   if (tables_dirty_) rebuild_tables();
   SolveHost* s = solve(slot);
   const int64_t npts = s->points();
   const double* src = dense;
   void* tmp = nullptr;
+  bool host_direct = false;
   if (!on_device) {
-    tmp = pool_.alloc((size_t)npts * 8);
-    cuda_check(cudaMemcpyAsync(tmp, dense, (size_t)npts * 8, cudaMemcpyHostToDevice, stream_), "H2D field");
-    src = (const double*)tmp;
+    if (const void* dp = locked_host_device_ptr(dense)) {
+      src = (const double*)dp;
+      host_direct = true;
+    } else {
+      tmp = pool_.alloc((size_t)npts * 8);
+      cuda_check(cudaMemcpyAsync(tmp, dense, (size_t)npts * 8, cudaMemcpyHostToDevice, stream_), "H2D field");
+      src = (const double*)tmp;
+    }
   }
   LAUNCH(launch_scatter(solve_tables(*s), src, which, 0, s->spec.n[0], s->spec.n[1], stream_), "scatter");
-  if (tmp) {
-    cuda_check(cudaStreamSynchronize(stream_), "sync");
-    pool_.release(tmp);
-  }
+  // a host buffer is the caller's again when the call returns
+  if (tmp || host_direct) cuda_check(cudaStreamSynchronize(stream_), "sync");
+  if (tmp) pool_.release(tmp);
 }
 
 void Workset::gather(int slot, double* dense, int on_device) {
@@ -506,16 +523,20 @@ void Workset::gather(int slot, double* dense, int on_device) {
   const int64_t npts = s->points();
   double* dst = dense;
   void* tmp = nullptr;
+  bool host_direct = false;
   if (!on_device) {
-    tmp = pool_.alloc((size_t)npts * 8);
-    dst = (double*)tmp;
+    if (const void* dp = locked_host_device_ptr(dense)) {
+      dst = (double*)dp;
+      host_direct = true;
+    } else {
+      tmp = pool_.alloc((size_t)npts * 8);
+      dst = (double*)tmp;
+    }
   }
   LAUNCH(launch_gather(solve_tables(*s), dst, 0, s->spec.n[0], s->spec.n[1], stream_), "gather");
-  if (tmp) {
-    cuda_check(cudaMemcpyAsync(dense, tmp, (size_t)npts * 8, cudaMemcpyDeviceToHost, stream_), "D2H field");
-    cuda_check(cudaStreamSynchronize(stream_), "sync");
-    pool_.release(tmp);
-  }
+  if (tmp) cuda_check(cudaMemcpyAsync(dense, tmp, (size_t)npts * 8, cudaMemcpyDeviceToHost, stream_), "D2H field");
+  if (tmp || host_direct) cuda_check(cudaStreamSynchronize(stream_), "sync");
+  if (tmp) pool_.release(tmp);
 }
 
 // Standalone exchange of the FP64 iterate x[(phase + kpar) & 1] for every
