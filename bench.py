@@ -215,8 +215,9 @@ def oracle_sample(p, sweeps):
 
 
 def cpu_baseline(p, name):
-    sweeps = {"poisson2d_8192": 50, "poisson2d_4096": 200, "laplace2d_256": 2000, "poisson3d_512": 20,
-              "poisson3d_256": 100}[name]
+    # about 10-15 s of CPU work on 16 cores; on 8192^2 the whole 1000-sweep step
+    sweeps = {"poisson2d_8192": 1000, "poisson2d_4096": 2000, "laplace2d_256": 100000, "poisson3d_512": 300,
+              "poisson3d_256": 2000}[name]
     glups, dt, cores = oracle_sample(p, sweeps)
     return {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
             "sample": f"{sweeps} sweeps of the full {'x'.join(map(str, p.dims))} grid with residual tests "
