@@ -130,10 +130,16 @@ jacobi_status jacobi_solve(jacobi_t ctx, double tol, int64_t max_sweeps, int64_t
                            double* final_rel);
 
 /* Copy the current iterate out (interior-dense) to host (on_device = 0) or
- * device memory.  Synchronises the stream for host output. */
+ * device memory.  Synchronises the stream for host output: the host buffer
+ * holds the field when the call returns.  A page-locked host buffer (pinned
+ * or registered) is written by the layout kernel directly; other host memory
+ * goes through a device staging buffer. */
 jacobi_status jacobi_get_field(jacobi_t ctx, double* out, int on_device);
 
-/* Replace the current iterate (interior-dense, host or device memory). */
+/* Replace the current iterate (interior-dense, host or device memory).  A
+ * host buffer may be reused as soon as the call returns (page-locked buffers
+ * are read by the layout kernel directly, other host memory through a
+ * staging copy). */
 jacobi_status jacobi_set_field(jacobi_t ctx, const double* in, int on_device);
 
 /* Replace the source term f (interior-dense, host or device memory). */

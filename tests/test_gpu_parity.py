@@ -408,3 +408,17 @@ def test_checkpoint_and_resume(dtype):
         # run restarts its inner sweeps from r of the saved field: the same
         # steps, bit for bit
         assert np.array_equal(resumed, full)
+
+
+@pytest.mark.parametrize("split", [0, 1])
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False)])
+def test_refine_3d_standalone_halo_matches_oracle(split, dtype, e16, r16):
+    """3D refinement with the standalone pack/unpack halo exchange, the outer
+    step fused or split, against the oracle's emulation."""
+    p = inputs.make_problem((30, 22, 19), (16, 8, 7), 57, boundary="uniform", source="normal", x0="zero")
+    st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, 20,
+                                             e_bf16=e16, r_bf16=r16)
+    with solver(p, dtype=dtype, refine_period=20, halo=1, outer_split=split) as s:
+        st, sw, rel = s.solve(1e-8, 10 ** 6)
+        x = s.field()
+    assert st == J.OK and sw == sw_o and np.array_equal(x, x_o)
