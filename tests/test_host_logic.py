@@ -79,3 +79,25 @@ def test_torch_allocator_trampolines_are_created_once():
     J.use_torch_allocator(False)
     J.use_torch_allocator(True)
     assert J._alloc_cb is a and J._free_cb is f
+
+
+@pytest.mark.parametrize("compiler,flags", [("gcc", ["-std=c99", "-x", "c"]), ("g++", ["-std=c++11", "-x", "c++"])])
+def test_header_compiles_as_plain_c_and_cpp(tmp_path, compiler, flags):
+    """include/jacobi.h is a self-contained C header (usable from C and C++
+    without CUDA or torch headers), with no warnings under -pedantic."""
+    import shutil
+    import subprocess
+    if shutil.which(compiler) is None:
+        pytest.skip(f"{compiler} not available")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "jacobi.h"\n'
+                   "int main(void) {\n"
+                   "  jacobi_t ctx = 0;\n"
+                   "  jacobi_boundary bc;\n"
+                   "  (void)ctx; (void)bc;\n"
+                   "  return (int)JACOBI_OK;\n"
+                   "}\n")
+    inc = os.path.join(ROOT, "include")
+    r = subprocess.run([compiler, *flags, "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, "-c", str(src),
+                        "-o", str(tmp_path / "use_header.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
