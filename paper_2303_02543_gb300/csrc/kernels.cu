@@ -17,7 +17,8 @@
 // The pair (E + N) of a point is the pair (W + S) of its diagonal neighbour
 // one row up and one column right (2D; in 3D the same holds along x and z),
 // so a warp marching along the last axis forms each such pair once and
-// passes it on: 3.5 FP64 additions per 2D update instead of 4.
+// passes it on: 3 FP64 additions per 2D update instead of 4, plus one edge
+// pair per warp row (per block row with the march items of k_f64_march).
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
