@@ -254,7 +254,9 @@ jacobi_status jacobi_batch_get_field(jacobi_t ctx, int i, double* out, int on_de
 typedef struct jacobi_server* jacobi_server_t;
 
 typedef struct {
-  int64_t submitted, admitted, completed, rejected; /* request counts */
+  /* request counts; rejected: refused at submit, or completed with
+   * JACOBI_ERR_OOM at admission */
+  int64_t submitted, admitted, completed, rejected;
   int64_t active, queued;                           /* solves on the GPU / waiting now */
   int64_t bytes_in_use, budget_bytes;               /* device memory of the arena */
   int64_t steps;                                    /* refinement steps run */
@@ -275,7 +277,8 @@ jacobi_status jacobi_server_create(jacobi_server_t* out, int dtype, int64_t hbm_
                                    void* cuda_stream);
 
 /* Options "refine_period", "schedule", "graph", "halo", "rows_low", "rows_f64"
- * (meaning as for contexts); JACOBI_ERR_BUSY once a request was submitted. */
+ * (meaning as for contexts); JACOBI_ERR_BUSY once any request was submitted
+ * (the first jacobi_server_submit fixes them). */
 jacobi_status jacobi_server_set_option(jacobi_server_t srv, const char* key, int64_t value);
 
 /* Queue one solve to relative residual tol (inputs are copied; thread-safe).
@@ -290,7 +293,11 @@ jacobi_status jacobi_server_submit(jacobi_server_t srv, const jacobi_problem* p,
 
 /* JACOBI_OK and the result (and, if field_out is not NULL, the interior-dense
  * field in host memory) when the request is done -- the ticket is then
- * forgotten; JACOBI_ERR_BUSY while it is queued or running. */
+ * forgotten; JACOBI_ERR_BUSY while it is queued or running.  out->status is
+ * the solve's outcome: JACOBI_OK, JACOBI_ERR_NOT_CONVERGED,
+ * JACOBI_ERR_DIVERGED, or JACOBI_ERR_OOM when its state did not fit even in
+ * the otherwise empty arena (nothing ran; field_out is left untouched; the
+ * request counts as rejected in the statistics). */
 jacobi_status jacobi_server_poll(jacobi_server_t srv, uint64_t ticket, jacobi_result* out, double* field_out);
 
 /* Block until the ticket is done or timeout_s elapses (JACOBI_ERR_BUSY). */

@@ -108,6 +108,37 @@ class Arena {
   std::mutex mu_;
 };
 
+// Page-locked host staging for the dense fields of admitted and retired
+// solves.  The layout kernels read and write it directly over the host link,
+// so neither admission nor retirement takes a device temporary from the arena
+// (a retirement must not fail for want of arena space).  It only grows: every
+// admission sizes it for its solve, so a retirement never allocates.
+class PinnedStage {
+ public:
+  ~PinnedStage() {
+    if (p_) cudaFreeHost(p_);
+  }
+  double* get(size_t n) {
+    if (n > n_) {
+      if (p_) cudaFreeHost(p_);
+      p_ = nullptr;
+      n_ = 0;
+      if (cudaMallocHost((void**)&p_, n * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        p_ = nullptr;
+        throw JErr{JACOBI_ERR_OOM, "page-locked host staging of " + std::to_string(n * sizeof(double)) +
+                                       " bytes failed"};
+      }
+      n_ = n;
+    }
+    return p_;
+  }
+
+ private:
+  double* p_ = nullptr;
+  size_t n_ = 0;
+};
+
 struct Request {
   uint64_t ticket = 0;
   ProblemSpec spec;
@@ -142,6 +173,7 @@ struct jacobi_server {
   cudaStream_t stream = nullptr;
   Options opt;
   Arena arena;
+  PinnedStage stage;                    // driver thread only
   Workset* ws[2] = {nullptr, nullptr};  // 2D, 3D
   std::map<int, Active> active[2];      // slot -> solve
   std::deque<Request> queue;
@@ -151,6 +183,7 @@ struct jacobi_server {
   std::condition_variable cv;
   std::thread driver;
   bool stop = false;
+  bool started = false;                 // a request was submitted: options are fixed
   std::string fatal;                    // set when the driver thread fails
   jacobi_server_stats stats;
   std::string err;
@@ -191,6 +224,7 @@ bool jacobi_server::step_once() {
   } pop_on_exit;
   // admission: first fit, in arrival order, within the arena
   std::vector<Request> admit;
+  const bool fresh = !ws[0] && !ws[1];  // the arena holds no workset state yet
   {
     std::lock_guard<std::mutex> lk(mu);
     int free_slots[2] = {max_slots - (int)active[0].size(), max_slots - (int)active[1].size()};
@@ -214,7 +248,21 @@ bool jacobi_server::step_once() {
     const int d = r.spec.ndim - 2;
     try {
       Workset* w = workset(r.spec.ndim);
-      const int slot = w->add_solve(r.spec);
+      // source and initial field go in through the page-locked stage; the
+      // request keeps its own copies in case it has to wait and retry
+      ProblemSpec spec = r.spec;
+      const size_t npts = (size_t)(spec.n[0] * spec.n[1] * spec.n[2]);
+      const size_t x0_at = spec.source ? (npts + 1) & ~(size_t)1 : 0;  // 16-byte aligned
+      double* st = stage.get(x0_at + npts);
+      if (spec.source) {
+        memcpy(st, spec.source, npts * sizeof(double));
+        spec.source = st;
+      }
+      if (spec.x0) {
+        memcpy(st + x0_at, spec.x0, npts * sizeof(double));
+        spec.x0 = st + x0_at;
+      }
+      const int slot = w->add_solve(spec);
       Active a;
       a.ticket = r.ticket;
       a.tol = r.tol;
@@ -225,14 +273,35 @@ bool jacobi_server::step_once() {
       std::lock_guard<std::mutex> lk(mu);
       stats.admitted += 1;
     } catch (const JErr& e) {
-      if (e.code == JACOBI_ERR_OOM || e.code == JACOBI_ERR_BUSY) {
-        // fragmentation: this request and the ones after it go back to the
-        // head of the queue, in order, and wait for a retirement
-        std::lock_guard<std::mutex> lk(mu);
-        for (size_t bi = admit.size(); bi-- > ai;) queue.push_front(std::move(admit[bi]));
-        break;
+      if (e.code != JACOBI_ERR_OOM && e.code != JACOBI_ERR_BUSY) throw;
+      // Out of arena (fragmentation, or workset tables larger than the margin).
+      // While some solve is resident, this request and the ones after it go
+      // back to the head of the queue, in order, and wait for a retirement.
+      // With nothing resident no retirement will come: empty worksets are
+      // freed and the request retried once from a clean arena; if it fails
+      // there too it can never fit, and it completes with JACOBI_ERR_OOM.
+      size_t from = ai;
+      if (active[0].empty() && active[1].empty()) {
+        if (!fresh) {
+          delete ws[0];
+          delete ws[1];
+          ws[0] = ws[1] = nullptr;
+        } else {
+          Done dn;
+          dn.res.status = JACOBI_ERR_OOM;
+          dn.res.reserved = 0;
+          dn.res.sweeps = 0;
+          dn.res.rel = std::nan("");
+          dn.res.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - r.t_submit).count();
+          std::lock_guard<std::mutex> lk(mu);
+          stats.rejected += 1;
+          done[r.ticket] = std::move(dn);
+          from = ai + 1;
+        }
       }
-      throw;
+      std::lock_guard<std::mutex> lk(mu);
+      for (size_t bi = admit.size(); bi-- > from;) queue.push_front(std::move(admit[bi]));
+      break;
     }
   }
   bool worked = false;
@@ -264,7 +333,9 @@ bool jacobi_server::step_once() {
       dn.res.rel = rel;
       dn.res.seconds = std::chrono::duration<double>(now - a.t_submit).count();
       dn.field.resize((size_t)a.points);
-      w->gather(kv.first, dn.field.data(), 0);
+      double* staged = stage.get((size_t)a.points);  // sized at admission: no allocation
+      w->gather(kv.first, staged, 0);
+      memcpy(dn.field.data(), staged, (size_t)a.points * sizeof(double));
       {
         std::lock_guard<std::mutex> lk(mu);
         stats.completed += 1;
@@ -376,8 +447,7 @@ jacobi_status jacobi_server_set_option(jacobi_server_t srv, const char* key, int
   if (!srv || !key) return JACOBI_ERR_INVALID;
   SRV_BEGIN
   std::lock_guard<std::mutex> lk(srv->mu);
-  if (srv->ws[0] || srv->ws[1] || !srv->queue.empty())
-    throw JErr{JACOBI_ERR_BUSY, "options are fixed once the first request is submitted"};
+  if (srv->started) throw JErr{JACOBI_ERR_BUSY, "options are fixed once the first request is submitted"};
   const std::string k(key);
   if (k == "refine_period") {
     if (value < 1 || value > 4096) throw JErr{JACOBI_ERR_INVALID, "refine_period must be in [1, 4096]"};
@@ -448,6 +518,7 @@ jacobi_status jacobi_server_submit(jacobi_server_t srv, const jacobi_problem* p,
   r.ticket = srv->next_ticket++;
   *ticket = r.ticket;
   srv->stats.submitted += 1;
+  srv->started = true;
   srv->queue.push_back(std::move(r));
   srv->cv.notify_all();
   return JACOBI_OK;

@@ -106,3 +106,79 @@ def test_short_request_overtakes_long_one():
         rb = srv.poll(tb)
     assert rs[0] == J.OK and rb[0] == J.OK and rs[3] < rb[3]
     assert np.array_equal(rs[4], alone(small)[2]) and np.array_equal(rb[4], alone(big)[2])
+
+
+def _smallest_accepted_budget(problem, lo=1 << 20, hi=64 << 20):
+    """Smallest budget (to 1 KiB) whose server accepts the request at submit."""
+    def accepted(budget):
+        with J.Server("f32_refine", budget_bytes=budget, max_slots=8, refine_period=K) as srv:
+            try:
+                srv.submit(problem, 1e300, 0)      # done at its first check
+            except J.JacobiError as e:
+                assert e.status == J.ERR_BUSY
+                return False
+            return True
+    assert accepted(hi) and not accepted(lo)
+    while hi - lo > 1024:
+        mid = (lo + hi) // 2
+        lo, hi = (lo, mid) if accepted(mid) else (mid, hi)
+    return hi
+
+
+def test_tight_arena_retires_and_admits_without_device_temporaries():
+    """Arenas around the size that holds three solves with almost nothing
+    left over: admission and retirement take no device memory from the arena,
+    so every solve completes, equal to the same solve run alone, however
+    little room the resident ones leave."""
+    p = inputs.make_problem((128, 128), (32, 32), 130, boundary="uniform", source="normal")
+    ref = alone(p)[2]
+    # the submit check accepts a request whose estimate b satisfies
+    # b + b/16 + 1 MiB <= budget
+    b = (_smallest_accepted_budget(p) - (1 << 20)) * 16 // 17
+    for delta in range(-32 << 10, 161 << 10, 16 << 10):
+        budget = 3 * b + b // 16 + delta
+        with J.Server("f32_refine", budget_bytes=budget, max_slots=8, refine_period=K) as srv:
+            tickets = [srv.submit(p, 1e-8, MAXS) for _ in range(4)]
+            for t in tickets:
+                assert srv.wait(t, 120.0), (delta, srv.stats())
+            results = [srv.poll(t) for t in tickets]
+            stats = srv.stats()
+        assert stats["completed"] == 4 and stats["rejected"] == 0, (delta, stats)
+        for r in results:
+            assert r[0] == J.OK
+            assert np.array_equal(r[4], ref)
+
+
+@pytest.mark.parametrize("max_slots", [1, 4096])
+def test_request_near_the_budget_completes_or_is_rejected_never_stalls(max_slots):
+    """A request accepted at submit is placed in an empty arena or, if its
+    state and the workset's tables do not fit there, completes with
+    JACOBI_ERR_OOM; the server neither stalls nor stops."""
+    p = inputs.make_problem((96, 80), (32, 32), 131, boundary="uniform", source="normal")
+    ref = alone(p)[2]
+    one = _smallest_accepted_budget(p)
+    for budget in (one, one + (64 << 10), one + (256 << 10)):
+        with J.Server("f32_refine", budget_bytes=budget, max_slots=max_slots, refine_period=K) as srv:
+            t = srv.submit(p, 1e-8, MAXS)
+            assert srv.wait(t, 60.0), srv.stats()
+            st, sw, rel, secs, field = srv.poll(t)
+            stats = srv.stats()
+            if st == J.OK:
+                assert np.array_equal(field, ref) and stats["rejected"] == 0
+            else:
+                assert st == J.ERR_OOM and sw == 0 and stats["rejected"] == 1
+            # the server still serves: a small request after it completes
+            q = inputs.make_problem((8, 8), (8, 8), 132, boundary="uniform", source="normal")
+            t2 = srv.submit(q, 1e-8, MAXS)
+            assert srv.wait(t2, 60.0), srv.stats()
+            assert srv.poll(t2)[0] == J.OK
+
+
+def test_options_are_fixed_by_the_first_submit():
+    with J.Server("f32_refine", budget_bytes=64 << 20, max_slots=4) as srv:
+        t = srv.submit(inputs.make_problem((16, 16), (16, 16), 133, source="normal"), 1e-8, MAXS)
+        assert J.load().jacobi_server_set_option(srv.h, b"refine_period", 10) == J.ERR_BUSY
+        assert srv.wait(t, 60.0)
+        srv.poll(t)
+        # still fixed after the queue drained and the solve retired
+        assert J.load().jacobi_server_set_option(srv.h, b"refine_period", 10) == J.ERR_BUSY
