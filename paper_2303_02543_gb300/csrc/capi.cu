@@ -176,6 +176,13 @@ jacobi_status jacobi_solve(jacobi_t ctx, double tol, int64_t max_sweeps, int64_t
   const SlotResult& r = res[ctx->slot];
   if (sweeps_done) *sweeps_done = r.sweeps;
   if (final_rel) *final_rel = r.rel;
+  if (r.status != JACOBI_OK) {
+    const std::string what = r.status == JACOBI_ERR_DIVERGED        ? "diverged"
+                             : r.status == JACOBI_ERR_NOT_CONVERGED ? "not converged"
+                                                                    : "stopped (status " + std::to_string(r.status) + ")";
+    ctx->err = what + " after " + std::to_string(r.sweeps) + " sweeps (relative residual " + std::to_string(r.rel) + ")";
+    t_err = ctx->err;
+  }
   return (jacobi_status)r.status;
   API_END(ctx)
 }

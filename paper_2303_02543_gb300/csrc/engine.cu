@@ -172,15 +172,32 @@ Workset::Workset(int ndim, int dtype, cudaStream_t stream, int capacity, bool r_
     : ndim_(ndim), dtype_(dtype), capacity_(capacity), r_bf16_(r_bf16 || dtype == 3), stream_(stream),
       cur_(stream), pool_(hooks ? *hooks : current_alloc_hooks(), stream) {
   solves_.assign(capacity, nullptr);
+  // device arrays belong to pool_, which frees them if a later step throws
   d_solves_ = (SolveDev*)pool_.alloc(sizeof(SolveDev) * capacity);
   d_rss_ = (double*)pool_.alloc(sizeof(double) * capacity);
   d_ticket_ = (uint32_t*)pool_.alloc(sizeof(uint32_t) * capacity);
   d_ctl_ = (SchedCtl*)pool_.alloc(sizeof(SchedCtl));
   d_slotctl_ = (int32_t*)pool_.alloc(sizeof(int32_t) * capacity);
-  cuda_check(cudaMallocHost((void**)&h_rss_, sizeof(double) * capacity), "cudaMallocHost");
-  cuda_check(cudaMallocHost((void**)&h_ctl_, sizeof(SchedCtl)), "cudaMallocHost");
-  cuda_check(cudaMallocHost((void**)&h_slotctl_, sizeof(int32_t) * capacity), "cudaMallocHost");
-  cuda_check(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking), "cudaStreamCreate");
+  try {
+    cuda_check(cudaMallocHost((void**)&h_rss_, sizeof(double) * capacity), "cudaMallocHost");
+    cuda_check(cudaMallocHost((void**)&h_ctl_, sizeof(SchedCtl)), "cudaMallocHost");
+    cuda_check(cudaMallocHost((void**)&h_slotctl_, sizeof(int32_t) * capacity), "cudaMallocHost");
+    cuda_check(cudaStreamCreateWithFlags(&cap_stream_, cudaStreamNonBlocking), "cudaStreamCreate");
+  } catch (...) {
+    free_host_side();  // the destructor does not run for a throwing constructor
+    throw;
+  }
+}
+
+void Workset::free_host_side() {
+  if (h_rss_) cudaFreeHost(h_rss_);
+  if (h_ctl_) cudaFreeHost(h_ctl_);
+  if (h_slotctl_) cudaFreeHost(h_slotctl_);
+  if (cap_stream_) cudaStreamDestroy(cap_stream_);
+  h_rss_ = nullptr;
+  h_ctl_ = nullptr;
+  h_slotctl_ = nullptr;
+  cap_stream_ = nullptr;
 }
 
 Workset::~Workset() {
@@ -194,10 +211,7 @@ Workset::~Workset() {
     }
   for (auto e : ev_free_) cudaEventDestroy(e);
   if (ev_open_) cudaEventDestroy(ev_open_);
-  if (h_rss_) cudaFreeHost(h_rss_);
-  if (h_ctl_) cudaFreeHost(h_ctl_);
-  if (h_slotctl_) cudaFreeHost(h_slotctl_);
-  if (cap_stream_) cudaStreamDestroy(cap_stream_);
+  free_host_side();
 }
 
 int Workset::live() const {

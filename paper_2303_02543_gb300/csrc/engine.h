@@ -131,6 +131,8 @@ class Workset {
   Workset(int ndim, int dtype, cudaStream_t stream, int capacity, bool r_bf16 = false,
           const AllocHooks* hooks = nullptr);
   ~Workset();
+  Workset(const Workset&) = delete;
+  Workset& operator=(const Workset&) = delete;
 
   // Adds a solve, uploads its inputs, computes ||b||; returns its slot.
   int add_solve(const ProblemSpec& p);
@@ -210,6 +212,7 @@ class Workset {
   cudaStream_t stream_;   // the caller's stream: everything ends up here
   cudaStream_t cur_;      // where launches are issued (stream_, or the capture stream)
   cudaStream_t cap_stream_ = nullptr;
+  void free_host_side();  // page-locked mirrors and the capture stream
   bool capturing_ = false;
   DevPool pool_;
   std::vector<SolveHost*> solves_;   // slot -> solve (nullptr when free)
