@@ -159,12 +159,23 @@ def _check(status, handle=None):
     return status
 
 
-def _ptr(a):
-    """Host numpy array or torch CUDA tensor -> (pointer, on_device)."""
-    if a is None:
-        return None, 0
+def _ptr(a, shape, writable=False):
+    """Host numpy array or torch tensor holding one interior-dense field of
+    `shape` -> (pointer, on_device).  The C side trusts the size, so a
+    mismatch in size, dtype, contiguity or device is refused here."""
+    n = int(np.prod(shape))
     if hasattr(a, "data_ptr"):  # torch tensor: device or (pinned) host memory
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous() or a.numel() != n:
+            raise ValueError(f"field tensor must be contiguous float64 with {n} elements "
+                             f"(got {a.dtype}, {tuple(a.shape)}, contiguous={a.is_contiguous()})")
+        if a.is_cuda and a.device.index != torch.cuda.current_device():
+            raise ValueError(f"field tensor is on {a.device}, the library runs on cuda:{torch.cuda.current_device()}")
         return ctypes.c_void_p(a.data_ptr()), 1 if a.is_cuda else 0
+    if not isinstance(a, np.ndarray) or a.dtype != np.float64 or not a.flags.c_contiguous or a.size != n:
+        raise ValueError(f"field array must be a C-contiguous float64 numpy array with {n} elements")
+    if writable and not a.flags.writeable:
+        raise ValueError("output field array is read-only")
     return ctypes.c_void_p(a.ctypes.data), 0
 
 
@@ -344,20 +355,20 @@ class Solver:
     def field(self, out=None):
         if out is None:
             out = np.empty(self.shape, dtype=np.float64)
-        p, dev = _ptr(out)
+        p, dev = _ptr(out, self.shape, writable=True)
         jacobi_get_field(self.h, p, dev)
         return out
 
     def set_field(self, x):
         if not hasattr(x, "data_ptr"):
             x = np.ascontiguousarray(x, dtype=np.float64)
-        p, dev = _ptr(x)
+        p, dev = _ptr(x, self.shape)
         jacobi_set_field(self.h, p, dev)
 
     def set_source(self, f):
         if not hasattr(f, "data_ptr"):
             f = np.ascontiguousarray(f, dtype=np.float64)
-        p, dev = _ptr(f)
+        p, dev = _ptr(f, self.shape)
         jacobi_set_source(self.h, p, dev)
 
     def set_option(self, key, value):
@@ -437,7 +448,7 @@ class Batch:
     def field(self, i, out=None):
         if out is None:
             out = np.empty(self.shapes[i], dtype=np.float64)
-        p, dev = _ptr(out)
+        p, dev = _ptr(out, self.shapes[i], writable=True)
         jacobi_batch_get_field(self.h, i, p, dev)
         return out
 

@@ -101,3 +101,26 @@ def test_header_compiles_as_plain_c_and_cpp(tmp_path, compiler, flags):
     r = subprocess.run([compiler, *flags, "-Wall", "-Wextra", "-Werror", "-pedantic", "-I", inc, "-c", str(src),
                         "-o", str(tmp_path / "use_header.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_binding_refuses_field_buffers_of_the_wrong_size_type_or_layout():
+    """The C side trusts a field buffer's size, so the binding checks it."""
+    import numpy as np
+    import torch
+    from paper_2303_02543_gb300 import jacobi as J
+    shape = (6, 5)
+    p, dev = J._ptr(np.zeros(shape), shape, writable=True)
+    assert p.value is not None and dev == 0
+    p, dev = J._ptr(torch.zeros(shape, dtype=torch.float64), shape)
+    assert dev == 0
+    bad = [np.zeros(shape, dtype=np.float32), np.zeros((6, 4)), np.zeros((5, 6)).T, [0.0] * 30,
+           torch.zeros(shape, dtype=torch.float32), torch.zeros((5, 6), dtype=torch.float64).t(),
+           torch.zeros((31,), dtype=torch.float64)]
+    for a in bad:
+        with pytest.raises(ValueError):
+            J._ptr(a, shape)
+    ro = np.zeros(shape)
+    ro.flags.writeable = False
+    J._ptr(ro, shape)
+    with pytest.raises(ValueError):
+        J._ptr(ro, shape, writable=True)
