@@ -301,17 +301,38 @@ def jacobi_last_error(h=None):
 
 # ---- convenience wrapper -------------------------------------------------
 
-def make_boundary(faces=None, value=None):
-    """Boundary struct from a list of face arrays (host) or a constant."""
+def face_sizes(dims):
+    """Values per Dirichlet face, in the header's face order (x-, x+, y-, y+,
+    z-, z+), for a grid of dims (nx, ny[, nz])."""
+    n = list(dims) + [1] * (3 - len(dims))
+    return [n[1] * n[2], n[1] * n[2], n[0] * n[2], n[0] * n[2], n[0] * n[1], n[0] * n[1]][:2 * len(dims)]
+
+
+def _host_input(v, n, what):
+    """Contiguous float64 copy (or view) of a host input that must hold n
+    values: the C side reads exactly n, so any other size is refused."""
+    a = np.ascontiguousarray(v, dtype=np.float64)
+    if a.size != n:
+        raise ValueError(f"{what} has {a.size} values; the grid needs {n}")
+    return a
+
+
+def make_boundary(faces=None, value=None, dims=None):
+    """Boundary struct from a list of face arrays (host) or a constant.  With
+    dims, every face's size is checked against the grid."""
     bc = Boundary()
     keep = []
     if faces is not None:
         bc.kind = BC_FACES
+        sizes = face_sizes(dims) if dims is not None else [None] * 6
+        if len(faces) > len(sizes):
+            raise ValueError(f"{len(faces)} faces given; the grid has {len(sizes)}")
         for i, f in enumerate(faces):
             if f is None:
                 bc.faces[i] = None
                 continue
-            arr = np.ascontiguousarray(f, dtype=np.float64)
+            arr = (np.ascontiguousarray(f, dtype=np.float64) if sizes[i] is None
+                   else _host_input(f, sizes[i], f"face {i}"))
             keep.append(arr)
             bc.faces[i] = arr.ctypes.data
     elif value is not None:
@@ -332,9 +353,10 @@ class Solver:
         self.dtype = DTYPES[dtype] if isinstance(dtype, str) else int(dtype)
         if torch_alloc:
             use_torch_allocator(True)
-        bc, keep = make_boundary(faces, bc_value)
-        src = None if source is None else np.ascontiguousarray(source, dtype=np.float64)
-        xx = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        bc, keep = make_boundary(faces, bc_value, self.dims)
+        npts = int(np.prod(self.dims))
+        src = None if source is None else _host_input(source, npts, "source")
+        xx = None if x0 is None else _host_input(x0, npts, "x0")
         self.stream = default_stream() if stream is None else stream
         self.h = jacobi_create(self.ndim, self.dims, block, self.dtype, bc,
                                None if src is None else src.ctypes.data,
@@ -415,23 +437,7 @@ class Batch:
         arr = (Problem * self.n)()
         keep = []
         for i, p in enumerate(problems):
-            dims = list(p.dims)
-            blk = list(p.block)
-            arr[i].ndim = len(dims)
-            for a in range(3):
-                arr[i].dims[a] = dims[a] if a < len(dims) else 1
-                arr[i].block[a] = blk[a] if a < len(blk) else 1
-            bc, k = make_boundary(p.faces)
-            keep.append(k)
-            arr[i].bc = bc
-            for name in ("source", "x0"):
-                v = getattr(p, name)
-                if v is None:
-                    setattr(arr[i], name, None)
-                else:
-                    a_ = np.ascontiguousarray(v, dtype=np.float64)
-                    keep.append(a_)
-                    setattr(arr[i], name, a_.ctypes.data)
+            arr[i] = _problem_struct(p, keep)
         self.stream = default_stream() if stream is None else stream
         self.h = jacobi_batch_create(arr, self.dtype, self.stream)
         del keep
@@ -485,15 +491,16 @@ def _problem_struct(p, keep):
     for a in range(3):
         ps.dims[a] = dims[a] if a < len(dims) else 1
         ps.block[a] = blk[a] if a < len(blk) else 1
-    bc, k = make_boundary(p.faces)
+    bc, k = make_boundary(p.faces, dims=dims)
     keep.append(k)
     ps.bc = bc
+    npts = int(np.prod(dims))
     for name in ("source", "x0"):
         v = getattr(p, name)
         if v is None:
             setattr(ps, name, None)
         else:
-            a_ = np.ascontiguousarray(v, dtype=np.float64)
+            a_ = _host_input(v, npts, name)
             keep.append(a_)
             setattr(ps, name, a_.ctypes.data)
     return ps

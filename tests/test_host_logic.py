@@ -124,3 +124,30 @@ def test_binding_refuses_field_buffers_of_the_wrong_size_type_or_layout():
     J._ptr(ro, shape)
     with pytest.raises(ValueError):
         J._ptr(ro, shape, writable=True)
+
+
+def test_binding_checks_host_input_sizes_against_the_grid():
+    """Source, initial field and Dirichlet faces are read by the C side for
+    exactly the grid's sizes; the binding refuses anything else."""
+    import numpy as np
+    from paper_2303_02543_gb300 import inputs
+    from paper_2303_02543_gb300 import jacobi as J
+    assert J.face_sizes((7, 5)) == [5, 5, 7, 7]
+    assert J.face_sizes((7, 5, 3)) == [15, 15, 21, 21, 35, 35]
+    for dims in ((7, 5), (7, 5, 3)):
+        p = inputs.make_problem(dims, dims, 3, boundary="random", source="normal", x0="uniform")
+        keep = []
+        ps = J._problem_struct(p, keep)          # the generator's own shapes pass
+        assert ps.ndim == len(dims) and ps.bc.kind == J.BC_FACES
+        for q in range(2 * len(dims)):
+            faces = list(p.faces)
+            faces[q] = np.zeros(faces[q].size + 1)
+            with pytest.raises(ValueError):
+                J.make_boundary(faces, dims=dims)
+        with pytest.raises(ValueError):
+            J.make_boundary(list(p.faces) + [np.zeros(1)] * (7 - len(p.faces)), dims=dims)
+        for name in ("source", "x0"):
+            q = inputs.make_problem(dims, dims, 3, boundary="random", source="normal", x0="uniform")
+            setattr(q, name, np.zeros(int(np.prod(dims)) - 1))
+            with pytest.raises(ValueError):
+                J._problem_struct(q, [])
