@@ -230,8 +230,10 @@ def run_reference(args, rank, world):
     if args.workload not in ("poisson2d_8192", "poisson2d_4096", "laplace2d_256", "poisson3d_512", "poisson3d_256"):
         args.workload = "poisson2d_8192"
     p, desc, _ = make_workload(args.workload)
-    sweeps = {"poisson2d_8192": 5, "poisson2d_4096": 20, "laplace2d_256": 500, "poisson3d_512": 2,
-              "poisson3d_256": 10}[args.workload]
+    # about a second per step on 16 cores, so that the oracle's per-call setup
+    # (ghosted copies of the inputs, two residual tests) is a small part of it
+    sweeps = {"poisson2d_8192": 100, "poisson2d_4096": 400, "laplace2d_256": 20000, "poisson3d_512": 20,
+              "poisson3d_256": 150}[args.workload]
     for _ in range(args.warmup):
         oracle_sample(p, sweeps)
     t0 = time.perf_counter()
