@@ -115,3 +115,18 @@ def test_fullsize_batch_256():
         return oracle.refine_solve(d, f, src, xw, 1e-300, steps * period, period)[1]
     for i in picks:
         check_samples(probs[i], fields[i], steps * (period + 1) + 1, run, 6, 75 + i)
+
+
+@pytest.mark.parametrize("form", ["f32_refine", "bf16_refine"])
+def test_time_to_tolerance_solves_pass_the_oracle(form):
+    """The time-to-tolerance workloads (512^2 in 2D, 128^3 in 3D, to relative
+    residual 1e-8, in the options the benchmark times): the oracle recomputes
+    the relative residual of each returned field from scratch."""
+    for p in (inputs.make_problem((512, 512), (128, 128), 2309, boundary="uniform", source="normal", x0="zero"),
+              inputs.poisson_3d(n=128, block=32)):
+        with J.Solver(p.dims, p.block, dtype=form, faces=p.faces, source=p.source, check_every=CHECK_EVERY,
+                      refine_period=20 if p.ndim == 3 else 50, schedule=1, graph=1, autotune=1) as s:
+            st, sw, rel = s.solve(1e-8, 10 ** 9)
+            x = s.field()
+        assert st == J.OK and rel <= 1e-8
+        assert oracle.relative_residual(p.dims, p.faces, p.source, x) <= 1e-8 * (1 + 1e-9)
