@@ -87,6 +87,9 @@ def parse():
     ap.add_argument("--rows-f64", type=int, default=0, help="lines per FP64 work item (0: library default)")
     ap.add_argument("--server-opts", default="", help="serving: server options as key=value,key=value")
     ap.add_argument("--block", default="", help="override the workload's block shape, e.g. 512,64,64")
+    ap.add_argument("--full-f64", action="store_true",
+                    help="tts3d_512: run the plain FP64 solve to 1e-8 (~11 min) instead of extrapolating it, "
+                         "which also gives the mixed forms' error against it")
     ap.add_argument("--ref-sweeps", type=int, default=0,
                     help="tts3d_512: sweep count of a refinement solve measured earlier, for the FP64 extrapolation "
                          "when only f64 runs")
@@ -478,7 +481,7 @@ def run_tts(args, rank, world, local):
     # 512^3 in plain FP64 would take ~15 minutes: its time is extrapolated
     # from 500 timed sweeps times the refinement's sweep count (the same
     # iteration in exact arithmetic), and labelled so
-    extrapolate = args.workload == "tts3d_512"
+    extrapolate = args.workload == "tts3d_512" and not args.full_f64
     if extrapolate and "f64" in forms:
         forms = [f for f in forms if f != "f64"] + ["f64"]
     out = {}

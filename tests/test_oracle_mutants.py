@@ -32,6 +32,8 @@ MUTANTS = {
                       "    m += k + 1;\n  }\n  store_interior(&G, a, x);\n  if (sweeps_out) *sweeps_out = m;"),
     # refinement that forgets to add the correction
     "refine_no_update": ("a[p] = a[p] + (double)e[p];", "a[p] = a[p] + 0.0 * (double)e[p];"),
+    # refinement whose update x += e is kept in float
+    "refine_float_update": ("a[p] = a[p] + (double)e[p];", "a[p] = (double)(float)(a[p] + (double)e[p]);"),
 }
 
 
@@ -47,6 +49,7 @@ def run_pins():
         "dense_res": lambda: pins.test_dense_residual_matches((7, 6)),
         "solve_rule": lambda: pins.test_solve_stops_at_first_checked_iterate(),
         "refine": lambda: pins.test_refine_converges_like_fp64(False, False),
+        "refine_deep": lambda: pins.test_refinement_reaches_fp64_accuracy_below_the_inner_precision((9, 7), False, False),
     }
     for name, fn in checks.items():
         try:

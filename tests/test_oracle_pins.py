@@ -305,6 +305,24 @@ def test_refine_converges_like_fp64(e_bf16, r_bf16):
     assert np.linalg.norm(x - x64) <= 1e-6 * np.linalg.norm(x64)
 
 
+@pytest.mark.parametrize("e_bf16,r_bf16", [(False, False), (True, False), (True, True)])
+@pytest.mark.parametrize("dims", [(9, 7), (5, 4, 6)])
+def test_refinement_reaches_fp64_accuracy_below_the_inner_precision(dims, e_bf16, r_bf16):
+    """With the residual and the update x += e in FP64, refinement keeps
+    converging after the correction falls below the inner type's precision
+    (float 2^-24, bfloat16 2^-9 relative): it reaches rel 1e-13, and x agrees
+    with the direct solve of the dense system to cond(A) * 1e-13, as plain
+    FP64 Jacobi does.  An update or residual kept in the inner type would
+    stall near its precision instead."""
+    faces, f, _ = tiny_problem(dims, 6)
+    A, b = dense.assemble(dims, faces, f)
+    xs = np.linalg.solve(A, b)
+    st, x, sw, rel = oracle.refine_solve(dims, faces, f, None, 1e-13, 10 ** 5, 10, e_bf16=e_bf16, r_bf16=r_bf16)
+    assert st == oracle.OK and rel <= 1e-13
+    cond = np.linalg.cond(A)
+    assert np.linalg.norm(x.reshape(-1) - xs) <= 4 * cond * 1e-13 * np.linalg.norm(xs)
+
+
 def test_refine_from_exact_solution_stops_at_once():
     u, faces, f = manufactured((12, 9), 21)
     st, x, sw, rel = oracle.refine_solve((12, 9), faces, f, u, 1e-12, 100, 10)
