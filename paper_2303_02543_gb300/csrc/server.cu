@@ -24,6 +24,7 @@
 
 #include "../../include/jacobi.h"
 #include "engine.h"
+#include "first_fit.h"
 
 using namespace jgb;
 
@@ -33,20 +34,20 @@ void set_thread_error(const std::string& msg);
 
 namespace {
 
-// First-fit arena over one device allocation, 256-byte granules.
+// First-fit arena over one device allocation (placement in first_fit.h).
 class Arena {
  public:
   bool init(size_t bytes, const AllocHooks& hooks, cudaStream_t s) {
     hooks_ = hooks;
     stream_ = s;
-    size_ = (bytes + 255) & ~(size_t)255;
-    if (hooks_.alloc) base_ = (char*)hooks_.alloc(size_, (void*)s, hooks_.user);
-    else if (cudaMalloc((void**)&base_, size_) != cudaSuccess) base_ = nullptr;
+    const size_t size = FirstFit::round_up(bytes);
+    if (hooks_.alloc) base_ = (char*)hooks_.alloc(size, (void*)s, hooks_.user);
+    else if (cudaMalloc((void**)&base_, size) != cudaSuccess) base_ = nullptr;
     if (!base_) {
       cudaGetLastError();
       return false;
     }
-    free_[0] = size_;
+    fit_.reset(size);
     return true;
   }
   ~Arena() {
@@ -57,44 +58,18 @@ class Arena {
   }
   void* alloc(size_t n) {
     std::lock_guard<std::mutex> lk(mu_);
-    n = (n + 255) & ~(size_t)255;
-    for (auto it = free_.begin(); it != free_.end(); ++it) {
-      if (it->second < n) continue;
-      const size_t off = it->first, sz = it->second;
-      free_.erase(it);
-      if (sz > n) free_[off + n] = sz - n;
-      used_[off] = n;
-      in_use_ += n;
-      return base_ + off;
-    }
-    return nullptr;
+    const size_t off = fit_.alloc(n);
+    return off == FirstFit::npos ? nullptr : base_ + off;
   }
   void release(void* p) {
     std::lock_guard<std::mutex> lk(mu_);
-    const size_t off = (size_t)((char*)p - base_);
-    auto u = used_.find(off);
-    if (u == used_.end()) return;
-    size_t n = u->second, start = off;
-    used_.erase(u);
-    in_use_ -= n;
-    auto nx = free_.lower_bound(off);
-    if (nx != free_.end() && nx->first == off + n) {
-      n += nx->second;
-      free_.erase(nx);
-    }
-    auto pv = free_.lower_bound(off);
-    if (pv != free_.begin()) {
-      --pv;
-      if (pv->first + pv->second == off) {
-        start = pv->first;
-        n += pv->second;
-        free_.erase(pv);
-      }
-    }
-    free_[start] = n;
+    fit_.release((size_t)((char*)p - base_));
   }
-  size_t in_use() const { return in_use_; }
-  size_t size() const { return size_; }
+  size_t in_use() {
+    std::lock_guard<std::mutex> lk(mu_);
+    return fit_.in_use();
+  }
+  size_t size() const { return fit_.size(); }
 
   static void* hook_alloc(size_t n, void*, void* user) { return ((Arena*)user)->alloc(n); }
   static void hook_free(void* p, void*, void* user) { ((Arena*)user)->release(p); }
@@ -103,8 +78,7 @@ class Arena {
   AllocHooks hooks_;
   cudaStream_t stream_ = nullptr;
   char* base_ = nullptr;
-  size_t size_ = 0, in_use_ = 0;
-  std::map<size_t, size_t> free_, used_;
+  FirstFit fit_;
   std::mutex mu_;
 };
 

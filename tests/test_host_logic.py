@@ -66,6 +66,19 @@ def test_exact_f64_helpers_match_ieee(tmp_path):
     assert "mismatches 0" in r.stdout
 
 
+def test_serving_arena_first_fit_matches_brute_force(tmp_path):
+    """The serving arena's placement (first_fit.h, host-only C++) against a
+    granule-by-granule first-fit model over random allocation and release
+    sequences."""
+    src = os.path.join(ROOT, "tests", "native", "first_fit_check.cpp")
+    exe = str(tmp_path / "first_fit_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-Wall", "-Wextra", "-Werror",
+                    "-I", os.path.join(ROOT, "paper_2303_02543_gb300", "csrc"), "-o", exe, src], check=True)
+    r = subprocess.run([exe, "200000"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "failures 0" in r.stdout
+
+
 def test_torch_allocator_trampolines_are_created_once():
     """A context keeps the allocator hooks it was created with; reinstalling
     must not free the ctypes trampolines those hooks point to."""
