@@ -206,15 +206,16 @@ def max_over_ranks(v, world):
 
 # ---- CPU oracle timing ------------------------------------------------------
 
-def oracle_sample(p, sweeps):
-    """Time the oracle (all host cores) on `sweeps` sweeps of the workload with
-    residual tests at both ends; returns (GLUP/s, seconds, threads)."""
+def oracle_sample(p, sweeps, threads=0):
+    """Time the oracle on `sweeps` sweeps of the workload with residual tests
+    at both ends, on all host cores (threads=0) or on `threads`; returns
+    (GLUP/s, seconds, threads used)."""
     import oracle
     oracle.build()
     t0 = time.perf_counter()
-    oracle.solve(p.dims, p.faces, p.source, p.x0, 1e-300, sweeps, CHECK_EVERY)
+    oracle.solve(p.dims, p.faces, p.source, p.x0, 1e-300, sweeps, CHECK_EVERY, threads=threads)
     dt = time.perf_counter() - t0
-    return p.points * sweeps / dt / 1e9, dt, oracle.max_threads()
+    return p.points * sweeps / dt / 1e9, dt, threads or oracle.max_threads()
 
 
 def cpu_baseline(p, name):
@@ -222,9 +223,14 @@ def cpu_baseline(p, name):
     sweeps = {"poisson2d_8192": 1000, "poisson2d_4096": 2000, "laplace2d_256": 100000, "poisson3d_512": 300,
               "poisson3d_256": 2000}[name]
     glups, dt, cores = oracle_sample(p, sweeps)
+    # one core, on a twentieth of the sweeps (a few seconds); taken last,
+    # because the oracle keeps the thread count it was last given
+    one, dt1, _ = oracle_sample(p, max(1, sweeps // 20), threads=1)
     return {"value": glups, "unit": "GLUP/s", "cores": cores, "kind": "oracle",
             "sample": f"{sweeps} sweeps of the full {'x'.join(map(str, p.dims))} grid with residual tests "
-                      f"before and after ({dt:.1f} s, OpenMP on {cores} threads)"}
+                      f"before and after ({dt:.1f} s, OpenMP on {cores} threads)",
+            "single_thread": {"value": one, "unit": "GLUP/s", "cores": 1,
+                              "sample": f"{max(1, sweeps // 20)} sweeps of the same grid on one thread ({dt1:.1f} s)"}}
 
 
 def run_reference(args, rank, world):
