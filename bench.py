@@ -2,7 +2,13 @@
 """Benchmark of the GB300 over-decomposed Jacobi library.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                    [--workload poisson2d_8192|laplace2d_256|poisson3d_512]
+                    [--workload poisson2d_8192|poisson3d_512|laplace2d_256|...]
+
+Other workloads (separate JSON lines, see --help): the profiling sizes
+poisson2d_4096 and poisson3d_256, time to 1e-8 (tts2d_512, tts3d_128,
+tts3d_512), the 256-solve batch (batched), Poisson arrivals into the server
+(serving) and the paper's 1024x1024x768 shape at four over-decomposition
+levels (paper3d_od).
 
 Workload (default): 2D 5-point Poisson, 8192x8192 FP64, over-decomposed into
 16x16 blocks of 512x512 with device-side halo exchange, seeded uniform[0,1)
@@ -18,8 +24,8 @@ solves are independent: weak scaling, no collective on the data path); the
 barrier and the max-over-ranks time only bracket the timed region.
 
 --impl reference times the CPU oracle (plain C, all host cores) on a bounded
-sample of the same workload: the paper's code is not available, so the oracle
-is the reference arm.
+sample of the same workload (100 of the 1000 sweeps per step at 8192^2): the
+paper's code is not available, so the oracle is the reference arm.
 """
 from __future__ import annotations
 
