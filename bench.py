@@ -185,12 +185,17 @@ def dist_setup(args):
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if world > 1:
-        import torch.distributed as dist
+        import datetime
+
         import torch
+        import torch.distributed as dist
         backend = "nccl" if torch.cuda.is_available() else "gloo"
         if torch.cuda.is_available():
             torch.cuda.set_device(local)
-        dist.init_process_group(backend=backend)
+        # a rank that fails or never arrives ends the others' next collective
+        # with an error after this long instead of leaving them waiting
+        timeout = datetime.timedelta(seconds=float(os.environ.get("JACOBI_PG_TIMEOUT_S", "900")))
+        dist.init_process_group(backend=backend, timeout=timeout)
     return rank, world, local
 
 

@@ -58,3 +58,42 @@ def test_reference_arm_under_torchrun_prints_once():
     assert len(lines) == 1
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2
+
+
+def _failing_worker(rank, world, port, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      LOCAL_RANK=str(rank), JACOBI_PG_TIMEOUT_S="20")
+    sys.path.insert(0, ROOT)
+    import time
+
+    import bench
+    bench.dist_setup(None)
+    if rank == 1:
+        os._exit(3)  # this rank fails between steps: it never reaches the barrier
+    t0 = time.time()
+    try:
+        bench.barrier(world)
+        out.put(("no error", time.time() - t0))
+    except Exception as e:  # noqa: BLE001 - the error itself is the result
+        out.put((type(e).__name__, time.time() - t0))
+    out.close()
+    out.join_thread()  # flush the result before leaving without teardown
+    os._exit(0)
+
+
+def test_a_failed_rank_ends_the_others_barrier_with_an_error():
+    """Failure detection on the host: when one rank dies between steps, the
+    surviving rank's next collective raises (peer gone, or the short
+    process-group timeout) instead of waiting for ever."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = free_port()
+    procs = [ctx.Process(target=_failing_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    for p in procs:
+        p.join(120)
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
+    kind, seconds = q.get(timeout=10)
+    assert kind != "no error" and seconds < 60
