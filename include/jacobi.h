@@ -125,7 +125,9 @@ jacobi_status jacobi_residual(jacobi_t ctx, double* rel, double* abs);
  * c, 2c, ... (c = option "check_every"; in refinement dtypes every outer step
  * of "refine_period" inner sweeps), at most max_sweeps sweeps.  Returns
  * JACOBI_OK, JACOBI_ERR_NOT_CONVERGED (the field is still valid) or
- * JACOBI_ERR_DIVERGED.  *sweeps_done / *final_rel may be NULL. */
+ * JACOBI_ERR_DIVERGED; for the last two jacobi_last_error(ctx) says after how
+ * many sweeps and at which residual it stopped.  *sweeps_done / *final_rel
+ * may be NULL. */
 jacobi_status jacobi_solve(jacobi_t ctx, double tol, int64_t max_sweeps, int64_t* sweeps_done,
                            double* final_rel);
 
@@ -224,7 +226,8 @@ typedef struct {
 
 /* Outcome of one problem. */
 typedef struct {
-  int32_t status;   /* JACOBI_OK, JACOBI_ERR_NOT_CONVERGED or JACOBI_ERR_DIVERGED */
+  int32_t status;   /* JACOBI_OK, JACOBI_ERR_NOT_CONVERGED or JACOBI_ERR_DIVERGED (server: also
+                       JACOBI_ERR_OOM, see jacobi_server_poll) */
   int32_t reserved;
   int64_t sweeps;   /* sweeps (inner sweeps for refinement) at the accepted iterate */
   double rel;       /* relative residual of the returned field */
