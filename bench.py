@@ -230,7 +230,7 @@ def oracle_sample(p, sweeps, threads=0):
 
 
 def cpu_baseline(p, name):
-    # about 10-15 s of CPU work on 16 cores; on 8192^2 the whole 1000-sweep step
+    # on 8192^2 the whole 1000-sweep step: about 7 s on 16 cores
     sweeps = {"poisson2d_8192": 1000, "poisson2d_4096": 2000, "laplace2d_256": 100000, "poisson3d_512": 300,
               "poisson3d_256": 2000}[name]
     glups, dt, cores = oracle_sample(p, sweeps)
