@@ -495,7 +495,7 @@ def run_tts(args, rank, world, local):
     else:
         p = inputs.poisson_3d(n=n, block=64 if n >= 256 else 32)
     forms = [f for f in args.forms.split(",") if f]
-    # 512^3 in plain FP64 would take ~15 minutes: its time is extrapolated
+    # 512^3 in plain FP64 takes ~11 minutes: by default its time is extrapolated
     # from 500 timed sweeps times the refinement's sweep count (the same
     # iteration in exact arithmetic), and labelled so
     extrapolate = args.workload == "tts3d_512" and not args.full_f64
