@@ -164,3 +164,44 @@ def test_binding_checks_host_input_sizes_against_the_grid():
             setattr(q, name, np.zeros(int(np.prod(dims)) - 1))
             with pytest.raises(ValueError):
                 J._problem_struct(q, [])
+
+
+def test_size_limits_and_empty_inputs_rejected_without_gpu():
+    """Empty grids, dimensions of 2^30 and beyond, more than 2^28 blocks, empty
+    or oversized batches, and out-of-range server settings are refused with
+    JACOBI_ERR_INVALID before any CUDA call (so also on a host without a GPU)."""
+    import ctypes
+    from paper_2303_02543_gb300 import build
+    from paper_2303_02543_gb300 import jacobi as J
+    build.build()
+    lib = J.load()
+    h = ctypes.c_void_p()
+    d3 = lambda *v: (ctypes.c_int64 * 3)(*v)  # noqa: E731
+    cases = [
+        (2, d3(0, 10, 1), d3(1, 1, 1)),                  # empty along x
+        (3, d3(10, 10, 0), d3(1, 1, 1)),                 # empty along z
+        (2, d3(1 << 30, 1, 1), d3(1 << 20, 1, 1)),       # dimension too large
+        (2, d3(1 << 29, 4, 1), d3(1, 1, 1)),             # 2^31 blocks
+        (3, d3(1 << 10, 1 << 10, 1 << 9), d3(1, 1, 2)),  # 2^28 blocks exactly
+        (2, d3(10, 10, 1), d3(0, 5, 1)),                 # empty block
+    ]
+    for nd, dims, blk in cases:
+        assert lib.jacobi_create(ctypes.byref(h), nd, dims, blk, 0, None, None, None, None) == J.ERR_INVALID
+        assert not h.value
+    assert lib.jacobi_batch_create(ctypes.byref(h), 0, None, 1, None) == J.ERR_INVALID
+    probs = (J.Problem * 1)()
+    assert lib.jacobi_batch_create(ctypes.byref(h), (1 << 20) + 1, probs, 1, None) == J.ERR_INVALID
+    assert lib.jacobi_batch_create(ctypes.byref(h), 1, probs, 1, None) == J.ERR_INVALID  # ndim 0
+    s = ctypes.c_void_p()
+    assert lib.jacobi_server_create(ctypes.byref(s), 0, 64 << 20, 4, None) == J.ERR_INVALID   # FP64 is not served
+    assert lib.jacobi_server_create(ctypes.byref(s), 1, (1 << 20) - 1, 4, None) == J.ERR_INVALID
+    assert lib.jacobi_server_create(ctypes.byref(s), 1, 64 << 20, 0, None) == J.ERR_INVALID
+    assert lib.jacobi_server_create(ctypes.byref(s), 1, 64 << 20, 4097, None) == J.ERR_INVALID
+    assert not s.value
+    x = ctypes.c_void_p(8)  # never dereferenced: validation fails first
+    assert lib.jacobi_residual_noalloc(2, d3(0, 4, 1), x, None, None, x, None) == J.ERR_INVALID
+    assert lib.jacobi_residual_noalloc(4, d3(4, 4, 4), x, None, None, x, None) == J.ERR_INVALID
+    assert lib.jacobi_residual_noalloc(2, d3(1 << 30, 4, 1), x, None, None, x, None) == J.ERR_INVALID
+    # beyond the fixed scratch: ceil(nx/64) * ceil(ny/8) partials > 2^20
+    assert lib.jacobi_residual_noalloc(2, d3(1 << 16, 1 << 15, 1), x, None, None, x, None) == J.ERR_INVALID
+    assert b"scratch" in lib.jacobi_last_error(None)
