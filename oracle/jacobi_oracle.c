@@ -208,9 +208,14 @@ static double rhs_ss(const grid_t* G, const double* a, const double* f) {
   return acc_value(&tot);
 }
 
+/* threads > 0: use that many OpenMP threads; 0: the runtime's default (all
+ * host cores unless OMP_NUM_THREADS says otherwise), restored even after an
+ * earlier call asked for fewer. */
 static void set_threads(int threads) {
 #ifdef _OPENMP
-  if (threads > 0) omp_set_num_threads(threads);
+  static int default_threads = 0;
+  if (default_threads == 0) default_threads = omp_get_max_threads();
+  omp_set_num_threads(threads > 0 ? threads : default_threads);
 #else
   (void)threads;
 #endif

@@ -34,6 +34,12 @@ MUTANTS = {
     "refine_no_update": ("a[p] = a[p] + (double)e[p];", "a[p] = a[p] + 0.0 * (double)e[p];"),
     # refinement whose update x += e is kept in float
     "refine_float_update": ("a[p] = a[p] + (double)e[p];", "a[p] = (double)(float)(a[p] + (double)e[p]);"),
+    # inner sweep of the correction with a wrong sign on one neighbour
+    "sweep_low_sign": ("(src[p + G->s[0]] + src[p + sl])", "(-src[p + G->s[0]] + src[p + sl])"),
+    # inner sweep that drops its right-hand side r
+    "sweep_low_no_rhs": ("const float t = s + r[didx(G, i, j, k)];", "const float t = s + 0.0f * r[didx(G, i, j, k)];"),
+    # inner sweep divided by 2d + 1 (a damped iteration with the wrong fixed point)
+    "sweep_low_divisor": ("const float v = t / two_d;", "const float v = t / (two_d + 1.0f);"),
 }
 
 
@@ -50,6 +56,7 @@ def run_pins():
         "solve_rule": lambda: pins.test_solve_stops_at_first_checked_iterate(),
         "refine": lambda: pins.test_refine_converges_like_fp64(False, False),
         "refine_deep": lambda: pins.test_refinement_reaches_fp64_accuracy_below_the_inner_precision((9, 7), False, False),
+        "refine_step": lambda: pins.test_refine_step_equals_plain_sweeps_in_exact_arithmetic((20, 14), False),
     }
     for name, fn in checks.items():
         try:

@@ -342,3 +342,29 @@ def test_golden_fixture_reproduces():
         assert x[y, xx] == float.fromhex(v)
     rss, bss = oracle.residual(p.dims, p.faces, p.source, x)
     assert rss == float.fromhex(doc["rss"]) and bss == float.fromhex(doc["bss"])
+
+
+@pytest.mark.parametrize("dims", [(12, 9), (6, 5, 4)])
+def test_non_finite_inputs_stop_the_solve_as_diverged(dims):
+    """The solve rule on a non-finite residual: a NaN in the source (so ||b||
+    and the residual are NaN) or an infinite initial value (an infinite
+    residual) stops the plain and the refinement solve at the first test,
+    after 0 sweeps, with JO_DIVERGED -- never as converged or capped.  So does
+    a NaN in one Dirichlet face value (it enters b)."""
+    p = inputs.make_problem(dims, dims, 14, boundary="uniform", source="normal", x0="uniform")
+    f_nan = p.source.copy()
+    f_nan.flat[f_nan.size // 2] = np.nan
+    x_inf = p.x0.copy()
+    x_inf.flat[1] = np.inf
+    for f, x0 in ((f_nan, p.x0), (p.source, x_inf)):
+        st, _, sw, rel = oracle.solve(p.dims, p.faces, f, x0, 1e-8, 100, 10)
+        assert st == oracle.DIVERGED and sw == 0 and not np.isfinite(rel)
+        st, _, sw, rel = oracle.refine_solve(p.dims, p.faces, f, x0, 1e-8, 100, 10)
+        assert st == oracle.DIVERGED and sw == 0 and not np.isfinite(rel)
+    faces = [g.copy() for g in p.faces]
+    faces[3].flat[0] = np.nan
+    st, _, sw, rel = oracle.solve(p.dims, faces, p.source, p.x0, 1e-8, 100, 10)
+    assert st == oracle.DIVERGED and sw == 0 and not np.isfinite(rel)
+    # the finite problem itself converges (the rule is not triggered by accident)
+    st, _, _, rel = oracle.solve(p.dims, p.faces, p.source, p.x0, 1e-3, 10 ** 5, 10)
+    assert st == oracle.OK and rel <= 1e-3
