@@ -311,6 +311,21 @@ jacobi_status jacobi_server_get_stats(jacobi_server_t srv, jacobi_server_stats* 
 /* Stops the driver thread and frees everything (pending requests are dropped). */
 void jacobi_server_destroy(jacobi_server_t srv);
 
+/* Measurement helper (not part of the method): the rate of the FP64 pipe.
+ * The plain FP64 sweep is bound by its FP64 additions on GB300 (the FP64 pipe
+ * is a small fraction of the FP32 rate), and every such addition is issued as
+ * an FMA with multiplier 1.0; this call times that instruction form in
+ * `chains` (1, 2, 4 or 8) independent dependency chains per thread, with
+ * ctas_per_sm (1..8) CTAs of 256 threads per SM, each thread issuing
+ * 8 * chains * iters operations (iters in [1, 2^24]).  *lane_ops_per_s gets
+ * the FP64 lane operations per second over the whole device.  With 8 chains
+ * and a full SM it is the pipe's throughput (the peak the FP64 sweep is
+ * reported against); with one chain it reflects the dependent-issue latency.
+ * Synchronises the stream; allocates no device memory.  Errors through
+ * jacobi_last_error(NULL). */
+jacobi_status jacobi_probe_fp64_rate(int chains, int ctas_per_sm, int64_t iters, double* lane_ops_per_s,
+                                     void* cuda_stream);
+
 /* Residual of an interior-dense field WITHOUT ANY DEVICE ALLOCATION.
  *
  * The paper has no counterpart to this call; it exists for callers that
@@ -334,10 +349,16 @@ void jacobi_server_destroy(jacobi_server_t srv);
  * variable of about 8 MiB that every GPU which loads the library keeps until
  * the process exits).  The grid must satisfy ceil(nx / 64) * ceil(ny / 8)
  * <= 2^20 in 2D and ceil(nx / 64) * ny * ceil(nz / 8) <= 2^20 in 3D (16384^2
- * and 512^3 fit); larger grids return JACOBI_ERR_INVALID before any GPU work.  The first call on a device looks up the array's
- * device address with that device current; make that first call before any
- * stream capture.  Every call shares the array, so calls that overlap on the
- * GPU (on different streams, or from different threads) race: order them.
+ * and 512^3 fit); larger grids return JACOBI_ERR_INVALID before any GPU work.
+ * The array has one instance per CUDA context that loads the library: the
+ * first call in a context (the device's primary context, a context made
+ * current through the driver API, or the primary context created again after
+ * a device reset) looks up its device address with that context current and
+ * keeps it for the context's later calls; make that first call before any
+ * stream capture.  Every call shares the array and it keeps the last call's
+ * contents (the reduction ticket is cleared by each call before use), so
+ * calls that overlap on the GPU (on different streams, or from different
+ * threads) race: order them.
  * Errors are reported through jacobi_last_error(NULL). */
 jacobi_status jacobi_residual_noalloc(int ndim, const int64_t dims[3], const double* x, const double* f,
                                       const double* const faces[6], double* rss_out, void* cuda_stream);

@@ -1001,8 +1001,10 @@ k_low_free(const WorkItem* __restrict__ items, int nitems, const BlockDev* __res
 // brought into shared memory by 1D bulk copies (cp.async.bulk, completion on
 // an mbarrier) up to kTmaStages - 2 lines ahead of the line being computed,
 // so the bytes in flight do not cost registers.  Lane 0 of each warp owns its
-// warp's ring; every wait is bounded and a wait that runs out sets bit 1 of
-// *status (JACOBI_ERR_TIMEOUT on the host).
+// warp's ring; every wait is bounded.  A wait that runs out sets bit 1 of
+// *status (JACOBI_ERR_TIMEOUT on the host; the outputs of that launch are then
+// invalid): the warp stops computing and issuing, waits (bounded) for the
+// copies it has in flight, and leaves.
 
 constexpr int kTmaStages = 6;
 
@@ -1091,6 +1093,7 @@ k_low_tma(const WorkItem* __restrict__ items, int nitems, const BlockDev* __rest
   };
   if (lane == 0)
     for (int L = L0; L <= L1 && L < L0 + NS; ++L) issue(L);
+  int issued = min(L1, L0 + NS - 1);  // last line whose copies were issued (warp-uniform)
   bool failed = false;
   auto wait_line = [&](int L) {
     const int st = (L - L0) % NS;
@@ -1147,18 +1150,21 @@ k_low_tma(const WorkItem* __restrict__ items, int nitems, const BlockDev* __rest
   float p[V], c[V], n[V];
   wait_line(L0);
   wait_line(m0);
+  failed = __any_sync(FULL_MASK, failed);
   if (any) {
     ld_stage(se + ((L0 - L0) % NS) * SEGW + V * lane, p);
     ld_stage(se + ((m0 - L0) % NS) * SEGW + V * lane, c);
   }
   float wv, ev, ge;
   edges(m0, wv, ev, ge);
-  for (int m = m0; m < mend; ++m) {
+  for (int m = m0; m < mend && !failed; ++m) {
     const int64_t lc = G.line(m);
     const int col = G.col(m);
     float wn = 0.f, en = 0.f, gn = 0.f;
     if (m + 1 < mend) edges(m + 1, wn, en, gn);
     wait_line(m + 1);
+    failed = __any_sync(FULL_MASK, failed);
+    if (failed) break;  // no new copies: only the ones in flight are drained below
     const int stc = (m - L0) % NS, stn = (m + 1 - L0) % NS;
     float rv[V], o[V];
 #pragma unroll
@@ -1182,7 +1188,10 @@ k_low_tma(const WorkItem* __restrict__ items, int nitems, const BlockDev* __rest
     }
     // line m-1's stage is free once every lane has read it: refill it
     __syncwarp();
-    if (lane == 0 && m - 1 + NS <= L1) issue(m - 1 + NS);
+    if (m - 1 + NS <= L1) {
+      if (lane == 0) issue(m - 1 + NS);
+      issued = m - 1 + NS;
+    }
     if (any) {
       stv<V>(ed + lc + x, o, nvalid);
       if constexpr (PUSH) {
@@ -1207,10 +1216,11 @@ k_low_tma(const WorkItem* __restrict__ items, int nitems, const BlockDev* __rest
     ev = en;
     ge = gn;
   }
-  if (__any_sync(FULL_MASK, failed)) {
+  if (failed) {
     if (lane == 0) atomicOr(status, 2u);
-    // let copies still in flight land before the warp's shared memory is released
-    for (int L = max(L0, L1 - NS + 1); L <= L1; ++L) {
+    // let the copies still in flight (at most the last NS lines issued, each
+    // stage's latest phase) land before the warp's shared memory is released
+    for (int L = max(L0, issued - NS + 1); L <= issued; ++L) {
       const int st = (L - L0) % NS;
       const uint32_t par = (uint32_t)(((L - L0) / NS) & 1);
       uint32_t iters = 0;

@@ -15,11 +15,13 @@
 // by the same warp tree, then the same two-level reduction.  Its result is
 // bit-identical to jacobi_residual on a monolithic context (and on any context
 // whose block extents are multiples of 64 along x and of 8 along the last axis).
+#include <cuda.h>  // CUcontext / CUresult types only: the driver is reached through the runtime
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/jacobi.h"
 
@@ -35,7 +37,6 @@ constexpr int kNaMaxChunks = (int)(kNaMaxParts / kNaChunk);
 constexpr int kNaThreads = 256;
 constexpr int kNaWarps = 8;
 constexpr int kNaGroup = 8;               // lines per partial along the last axis (as the context kernels)
-constexpr int kMaxDevices = 64;
 
 struct NaScratch {
   double part[kNaMaxParts];
@@ -45,10 +46,49 @@ struct NaScratch {
 
 static __device__ __align__(256) NaScratch g_na_scratch;
 
-// Device address of g_na_scratch per device ordinal (the host symbol is only a
-// stand-in and must never be handed to a kernel).
+// Device address of g_na_scratch per CUDA context.  A __device__ variable
+// has one instance per context that loads the module, so the address belongs
+// to the context, not to the device: a context made current through the
+// driver API, or the primary context re-created after a reset, has its own.
+// The cache is keyed by the context's unique ID (cuCtxGetId: never reused
+// within a process, unlike a context handle).  The host symbol itself is only
+// a stand-in and must never be handed to a kernel.
+struct NaAddr {
+  unsigned long long ctx_id;
+  NaScratch* addr;
+};
 std::mutex g_na_mu;
-NaScratch* g_na_addr[kMaxDevices] = {};
+std::vector<NaAddr> g_na_addr;
+constexpr size_t kNaMaxContexts = 256;  // entries of contexts long gone are dropped beyond this
+
+using PfnCtxGetCurrent = CUresult (*)(CUcontext*);
+using PfnCtxGetId = CUresult (*)(CUcontext, unsigned long long*);
+
+// ID of the current context through driver entry points fetched by the
+// runtime (the library does not link the driver library itself).  False when
+// the driver offers no such call; the caller then looks the address up on
+// every call.
+bool current_context_id(unsigned long long* id) {
+  static PfnCtxGetCurrent get_cur = nullptr;
+  static PfnCtxGetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 4000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_cur = (PfnCtxGetCurrent)f;
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (PfnCtxGetId)f;
+    (void)cudaGetLastError();
+  });
+  if (!get_cur || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_cur(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
 
 struct NaFaces {
   const double* f[6];
@@ -180,27 +220,41 @@ extern "C" jacobi_status jacobi_residual_noalloc(int ndim, const int64_t dims[3]
     return na_fail(JACOBI_ERR_INVALID, "every dimension must be in [1, 2^30)");
   const int64_t segs = (nx + 63) / 64;
   const int64_t ext = ndim == 2 ? ny : nz;
-  const int64_t nparts = segs * ((ext + kNaGroup - 1) / kNaGroup) * (ndim == 3 ? ny : 1);
-  if (nparts > kNaMaxParts)
-    return na_fail(JACOBI_ERR_INVALID,
-                   "grid too large for the fixed scratch: ceil(nx / 64) * ceil(n_last / 8) * (3D: ny) must be <= " +
-                       std::to_string(kNaMaxParts));
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return na_fail(JACOBI_ERR_CUDA, std::string("cudaGetDevice: ") + cudaGetErrorString(e));
-  if (dev < 0 || dev >= kMaxDevices) return na_fail(JACOBI_ERR_INVALID, "device ordinal out of range");
+  const int64_t groups = (ext + kNaGroup - 1) / kNaGroup;
+  // the count of partials, each factor checked before it multiplies (in 3D
+  // the plain product of three dimensions below 2^30 can pass 2^63)
+  const std::string too_big =
+      "grid too large for the fixed scratch: ceil(nx / 64) * ceil(n_last / 8) * (3D: ny) must be <= " +
+      std::to_string(kNaMaxParts);
+  if (segs > kNaMaxParts / groups) return na_fail(JACOBI_ERR_INVALID, too_big);
+  int64_t nparts = segs * groups;
+  if (ndim == 3) {
+    if (nparts > kNaMaxParts / ny) return na_fail(JACOBI_ERR_INVALID, too_big);
+    nparts *= ny;
+  }
+  if (nparts > kNaMaxParts) return na_fail(JACOBI_ERR_INVALID, too_big);
+  cudaError_t e = cudaSuccess;
   NaScratch* S = nullptr;
   {
+    // set-up once per CUDA context, with that context current: the device
+    // address of the scratch array in this context
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_addr[dev]) {
-      // once per device, with that device current
+    unsigned long long id = 0;
+    const bool keyed = current_context_id(&id);
+    if (keyed)
+      for (const NaAddr& a : g_na_addr)
+        if (a.ctx_id == id) S = a.addr;
+    if (!S) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_na_scratch);
       if (e != cudaSuccess)
         return na_fail(JACOBI_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      g_na_addr[dev] = (NaScratch*)p;
+      S = (NaScratch*)p;
+      if (keyed) {
+        if (g_na_addr.size() >= kNaMaxContexts) g_na_addr.clear();
+        g_na_addr.push_back(NaAddr{id, S});
+      }
     }
-    S = g_na_addr[dev];
   }
   cudaStream_t st = (cudaStream_t)cuda_stream;
   NaFaces g;

@@ -29,7 +29,7 @@ OK, ERR_INVALID, ERR_OOM, ERR_CUDA, ERR_NOT_CONVERGED, ERR_DIVERGED, ERR_TIMEOUT
 EXPORTS = ["jacobi_set_allocator", "jacobi_create", "jacobi_sweep", "jacobi_residual", "jacobi_solve",
            "jacobi_get_field", "jacobi_set_field", "jacobi_set_source", "jacobi_set_option",
            "jacobi_get_option", "jacobi_profile", "jacobi_device_bytes", "jacobi_destroy",
-           "jacobi_last_error", "jacobi_version", "jacobi_residual_noalloc",
+           "jacobi_last_error", "jacobi_version", "jacobi_residual_noalloc", "jacobi_probe_fp64_rate",
            "jacobi_batch_create", "jacobi_batch_solve", "jacobi_batch_get_field",
            "jacobi_server_create", "jacobi_server_set_option", "jacobi_server_submit", "jacobi_server_poll",
            "jacobi_server_wait", "jacobi_server_get_stats", "jacobi_server_destroy"]
@@ -100,6 +100,7 @@ def load(path: str | None = None):
         "jacobi_last_error": (ctypes.c_char_p, [vp]),
         "jacobi_version": (ctypes.c_int, []),
         "jacobi_residual_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, vp, vp, ctypes.POINTER(vp), vp, vp]),
+        "jacobi_probe_fp64_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, i64, dp, vp]),
         "jacobi_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(Problem),
                                                 ctypes.c_int, vp]),
         "jacobi_batch_solve": (ctypes.c_int, [vp, ctypes.c_double, i64, ctypes.POINTER(Result)]),
@@ -273,6 +274,14 @@ def jacobi_residual_noalloc(ndim, dims, x_ptr, f_ptr, face_ptrs, rss_ptr, stream
     if face_ptrs is not None:
         fp = (ctypes.c_void_p * 6)(*(list(face_ptrs) + [None] * (6 - len(face_ptrs))))
     return _check(load().jacobi_residual_noalloc(int(ndim), d, x_ptr, f_ptr, fp, rss_ptr, stream), None)
+
+
+def jacobi_probe_fp64_rate(chains=8, ctas_per_sm=8, iters=4096, stream=None):
+    """FP64 lane operations per second of fma.rn.f64 (multiplier 1.0, the
+    form of every FP64 addition in the sweeps) on the current device."""
+    v = ctypes.c_double()
+    _check(load().jacobi_probe_fp64_rate(int(chains), int(ctas_per_sm), int(iters), ctypes.byref(v), stream), None)
+    return v.value
 
 
 def jacobi_batch_create(problems, dtype, stream=None):

@@ -218,14 +218,22 @@ def test_refine_matches_oracle_emulation(dtype, e16, r16, dims, block):
     assert np.array_equal(x, x_o)
 
 
-def test_refine_r_bf16_converges():
-    p = inputs.make_problem((50, 40), (25, 20), 51, boundary="uniform", source="normal", x0="zero")
-    with J.Solver(p.dims, p.block, dtype="bf16_refine", faces=p.faces, source=p.source) as s:
-        pass
-    # r_bf16 is fixed at creation; exercised through the oracle emulation pin on the CPU
+@pytest.mark.parametrize("halo", [0, 1])
+def test_refine_r_bf16_2d_matches_oracle_emulation(halo):
+    """e and r both stored as bfloat16, 2D blocks with remainders, the halo of
+    e exchanged by the fused push or by the standalone pack/unpack kernels:
+    same inner-sweep count and the same field bits as the oracle's emulation,
+    and a relative residual <= 1e-8 by the oracle."""
+    p = inputs.make_problem((50, 40), (24, 15), 51, boundary="uniform", source="normal", x0="zero")
     st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, 20,
                                              e_bf16=True, r_bf16=True)
-    assert st_o == oracle.OK
+    with solver(p, dtype="bf16r16_refine", refine_period=20, halo=halo) as s:
+        st, sw, rel = s.solve(1e-8, 10 ** 6)
+        x = s.field()
+    assert st == J.OK and st_o == oracle.OK
+    assert sw == sw_o
+    assert np.array_equal(x, x_o)
+    assert oracle.relative_residual(p.dims, p.faces, p.source, x) <= 1e-8
 
 
 def test_refine_sweep_then_field_is_updated():

@@ -205,3 +205,15 @@ def test_size_limits_and_empty_inputs_rejected_without_gpu():
     # beyond the fixed scratch: ceil(nx/64) * ceil(ny/8) partials > 2^20
     assert lib.jacobi_residual_noalloc(2, d3(1 << 16, 1 << 15, 1), x, None, None, x, None) == J.ERR_INVALID
     assert b"scratch" in lib.jacobi_last_error(None)
+    # 3D dimensions just below 2^30: the partial count (~2^81) must not wrap
+    # around int64 and slip past the scratch limit
+    big = (1 << 30) - 1
+    assert lib.jacobi_residual_noalloc(3, d3(big, big, big), x, None, None, x, None) == J.ERR_INVALID
+    assert b"scratch" in lib.jacobi_last_error(None)
+    assert lib.jacobi_residual_noalloc(3, d3(64, big, 8), x, None, None, x, None) == J.ERR_INVALID
+    # the FP64 rate probe checks its arguments before any CUDA call
+    v = ctypes.c_double()
+    assert lib.jacobi_probe_fp64_rate(3, 1, 16, ctypes.byref(v), None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(8, 0, 16, ctypes.byref(v), None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(8, 1, 0, ctypes.byref(v), None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(8, 1, 16, None, None) == J.ERR_INVALID
