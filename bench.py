@@ -129,13 +129,14 @@ def measured_peaks():
 
 
 def fp64_peak(stream):
-    """Measured FP64 pipe rate (G lane operations/s) of fma.rn.f64 with
-    multiplier 1.0 -- the form of every FP64 addition in the sweeps -- in 8
-    independent chains per thread on a full device: best of three."""
+    """Measured FP64 pipe rate (G lane operations/s) of fma.rn.f64 with the
+    multiplier 1.0 in a register -- the form of every FP64 addition in the
+    sweeps, and the fastest FP64 instruction form on GB300 -- in 8 independent
+    chains per thread on a full device: best of three."""
     from paper_2303_02543_gb300 import jacobi as J
     try:
-        best = max(J.jacobi_probe_fp64_rate(8, 8, 8192, stream) for _ in range(3))
-        return best / 1e9, "measured: fma.rn.f64 probe (8 chains/thread, 8 CTAs/SM), best of 3"
+        best = max(J.jacobi_probe_fp64_rate(1, 8, 8, 8192, stream) for _ in range(3))
+        return best / 1e9, "measured: fma.rn.f64 probe, register multiplier (8 chains/thread, 8 CTAs/SM), best of 3"
     except J.JacobiError as e:
         return FP64_ADD_PEAK_NOMINAL_G, f"nominal (probe failed: {e})"
 

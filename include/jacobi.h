@@ -314,16 +314,21 @@ void jacobi_server_destroy(jacobi_server_t srv);
 /* Measurement helper (not part of the method): the rate of the FP64 pipe.
  * The plain FP64 sweep is bound by its FP64 additions on GB300 (the FP64 pipe
  * is a small fraction of the FP32 rate), and every such addition is issued as
- * an FMA with multiplier 1.0; this call times that instruction form in
- * `chains` (1, 2, 4 or 8) independent dependency chains per thread, with
+ * an FMA with multiplier 1.0.  This call times one instruction form:
+ *   form 0  fma.rn.f64 with the immediate multiplier 1.0
+ *   form 1  fma.rn.f64 with the multiplier 1.0 held in a register
+ *   form 2  add.rn.f64
+ *   form 3  mul.rn.f64 by a register
+ *   form 4  fma.rn.f64 with the multiplier 1.0 read from constant memory
+ * in `chains` (1, 2, 4 or 8) independent dependency chains per thread, with
  * ctas_per_sm (1..8) CTAs of 256 threads per SM, each thread issuing
  * 8 * chains * iters operations (iters in [1, 2^24]).  *lane_ops_per_s gets
  * the FP64 lane operations per second over the whole device.  With 8 chains
- * and a full SM it is the pipe's throughput (the peak the FP64 sweep is
- * reported against); with one chain it reflects the dependent-issue latency.
- * Synchronises the stream; allocates no device memory.  Errors through
- * jacobi_last_error(NULL). */
-jacobi_status jacobi_probe_fp64_rate(int chains, int ctas_per_sm, int64_t iters, double* lane_ops_per_s,
+ * and a full SM it is the pipe's throughput for that form (the peak the FP64
+ * sweep is reported against); with one chain it also reflects the
+ * dependent-issue latency.  Synchronises the stream; allocates no device
+ * memory.  Errors through jacobi_last_error(NULL). */
+jacobi_status jacobi_probe_fp64_rate(int form, int chains, int ctas_per_sm, int64_t iters, double* lane_ops_per_s,
                                      void* cuda_stream);
 
 /* Residual of an interior-dense field WITHOUT ANY DEVICE ALLOCATION.

@@ -37,14 +37,28 @@ namespace jgb {
 
 // a + b rounded to nearest even, issued as fma(a, 1, b): the product a * 1 is
 // exact, so the result is bit-identical to __dadd_rn(a, b) for every input.
-// On GB300 the FMA issues faster than the FP64 add (about 1.9 versus 1.55 per
-// clock per SM, measured).  It is written in PTX because the compiler turns
-// fma(a, 1.0, b) in C++ back into an add.
+// It is written in PTX because the compiler would turn fma(a, 1.0, b) back
+// into an add.
+//
+// On GB300 an FP64 FMA whose multiplier is a register issues at the full FP64
+// rate (2.0 lanes per clock per SM, measured 628 G/s), while the FP64 add, the
+// FP64 multiply and an FMA whose multiplier is an immediate or a constant-bank
+// operand issue at 1.68 (529 G/s).  The hot kernels therefore call dadd1 with
+// `one` = 1.0 loaded once per thread from global memory (load_one), so that
+// the compiler cannot see its value and fold it into an immediate; dadd is
+// the plain form for the cold paths.
 __device__ __forceinline__ double dadd(double a, double b) {
   double r;
   asm("fma.rn.f64 %0, %1, 0d3FF0000000000000, %2;" : "=d"(r) : "d"(a), "d"(b));
   return r;
 }
+__device__ __forceinline__ double dadd1(double a, double b, double one) {
+  double r;
+  asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(one), "d"(b));
+  return r;
+}
+__device__ double g_fp64_one = 1.0;
+__device__ __forceinline__ double load_one() { return __ldg(&g_fp64_one); }
 
 // The rare-case paths behind the warp votes below are out-of-line calls: the
 // compiler would otherwise compute them for every point and select afterwards,
@@ -289,6 +303,7 @@ struct F64Src {
   const double* __restrict__ x;
   const TE* __restrict__ e;
   bool apply;
+  double unit;  // 1.0 in a register (see dadd1)
 
   struct Raw1 {
     double v;
@@ -310,7 +325,7 @@ struct F64Src {
   // operation may appear here, so the conversion is the plain instruction.
   __device__ __forceinline__ double fin1(const Raw1& r) const {
     if constexpr (MODE == kModeOuter) {
-      if (apply) return dadd(r.v, (double)r.e);
+      if (apply) return dadd1(r.v, (double)r.e, unit);
     }
     return r.v;
   }
@@ -344,8 +359,8 @@ struct F64Src {
     b = r.b;
     if constexpr (MODE == kModeOuter) {
       if (apply) {  // uniform: one flag per solve
-        a = dadd(a, f2d(r.ea));
-        b = dadd(b, f2d(r.eb));
+        a = dadd1(a, f2d(r.ea), unit);
+        b = dadd1(b, f2d(r.eb), unit);
       }
     }
   }
@@ -440,7 +455,10 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   const BlockDev B = blocks[it.block];
   const SolveDev* S = solves + B.solve;
   const int par = (S->phase + kpar) & 1;
+  const double one = load_one();
+  auto add = [one](double u, double v) { return dadd1(u, v, one); };
   F64Src<MODE, TE, COH> src;
+  src.unit = one;
   src.x = S->x[par];
   src.e = MODE == kModeOuter ? reinterpret_cast<const TE*>(S->e[epar]) : nullptr;
   src.apply = MODE == kModeOuter && S->apply_e;
@@ -515,8 +533,8 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
       double s0, s1, q0, q1;
       src.fin2(a.sr, s0, s1);
       src.fin2(a.qr, q0, q1);
-      a.sn0 = dadd(s0, q0);
-      a.sn1 = dadd(s1, q1);
+      a.sn0 = add(s0, q0);
+      a.sn1 = add(s1, q1);
     }
   };
 
@@ -533,8 +551,8 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   if (lane == 31 && east_inner) pE = src.one(G.line(m0 - 1) + x + 2);
   if (last0) c1 = a.eg;
   double qacc = 0.0;  // residual: this lane's sum of r^2 over the current group
-  double A0p = dadd(p1, c0);
-  double A1p = dadd(pE, c1);
+  double A0p = add(p1, c0);
+  double A1p = add(pE, c1);
 
   for (int m = m0; m < mend; ++m) {
     const int64_t lc = G.line(m);
@@ -557,27 +575,27 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
       if (xs > 0) {
         if (lane == 0) bw = rd[m - m0];
       } else if (lane == 0) {
-        bw = dadd(a.wv, p0);
+        bw = add(a.wv, p0);
       }
     } else if constexpr (EMU >= 3) {
       const double be = dadd_int(a.wv, p0);
       if (lane == 0) bw = be;
     } else {
-      if (lane == 0) bw = dadd(a.wv, p0);
+      if (lane == 0) bw = add(a.wv, p0);
     }
-    const double A0 = dadd(c1, n0);  // P(m, x)   = c[x+1] + n[x]
-    const double A1 = dadd(e1, n1);  // P(m, x+1) = c[x+2] + n[x+1]
-    double t0 = dadd(bw, A0), t1 = dadd(A0p, A1);
+    const double A0 = add(c1, n0);  // P(m, x)   = c[x+1] + n[x]
+    const double A1 = add(e1, n1);  // P(m, x+1) = c[x+2] + n[x+1]
+    double t0 = add(bw, A0), t1 = add(A0p, A1);
     if constexpr (DIM == 3) {
-      t0 = dadd(t0, a.sn0);
-      t1 = dadd(t1, a.sn1);
+      t0 = add(t0, a.sn0);
+      t1 = add(t1, a.sn1);
     }
     if constexpr (EMU >= 2) {
       t0 = dadd_int(t0, a.f0);
       t1 = dadd_int(t1, a.f1);
     } else {
-      t0 = dadd(t0, a.f0);
-      t1 = dadd(t1, a.f1);
+      t0 = add(t0, a.f0);
+      t1 = add(t1, a.f1);
     }
 
     if constexpr (WRITE) {
@@ -622,8 +640,8 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
     }
     if constexpr (RESID || STORE_R) {
       // t - (2d) x as fma(t, 1, -(2d) x): the same rounding as the subtraction
-      const double r0 = dadd(t0, -twod_x<DIM>(c0));
-      const double r1 = dadd(t1, -twod_x<DIM>(c1));
+      const double r0 = add(t0, -twod_x<DIM>(c0));
+      const double r1 = add(t1, -twod_x<DIM>(c1));
       if constexpr (STORE_R) {
         const float rf0 = d2f(r0), rf1 = d2f(r1);
         if (v1) {
@@ -642,7 +660,7 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
         if ((m + 1) % kResGroup == 0 || m + 1 == G.extent) {
           double q = qacc;
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) q = dadd(q, __shfl_xor_sync(FULL_MASK, q, o));
+          for (int o = 16; o > 0; o >>= 1) q = add(q, __shfl_xor_sync(FULL_MASK, q, o));
           if (lane == 0) {
             const int64_t grp = (int64_t)B.pg + m / kResGroup;
             const int64_t row = DIM == 2 ? grp : grp * S->ny + (B.oy + y);

@@ -25,21 +25,38 @@ namespace {
 constexpr int kProbeThreads = 256;
 
 // Sink for the chains' results (never read by the host: it only keeps the
-// arithmetic from being removed).
+// arithmetic from being removed) and the multiplier 1.0 read at run time (so
+// the compiler cannot see its value and fold it into an immediate).
 __device__ double g_probe_sink;
+__device__ double g_probe_one = 1.0;
+__constant__ double c_probe_one = 1.0;
 
-template <int CH>
-__global__ void __launch_bounds__(kProbeThreads) k_fp64_fma_rate(int iters, double seed) {
+// FORM 0: fma.rn.f64 with the immediate multiplier 1.0; 1: fma.rn.f64 with
+// the multiplier 1.0 in a register; 2: add.f64; 3: mul.f64 by a register;
+// 4: fma.rn.f64 with the multiplier 1.0 read from constant memory.
+template <int CH, int FORM>
+__global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(int iters, double seed) {
   double a[CH];
 #pragma unroll
   for (int c = 0; c < CH; ++c) a[c] = seed * (double)(threadIdx.x + 1 + c);
   const double b = seed * 1e-3;
+  const double one = __ldg(&g_probe_one);
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
 #pragma unroll
-      for (int c = 0; c < CH; ++c)
-        asm volatile("fma.rn.f64 %0, %0, 0d3FF0000000000000, %1;" : "+d"(a[c]) : "d"(b));
+      for (int c = 0; c < CH; ++c) {
+        if constexpr (FORM == 0)
+          asm volatile("fma.rn.f64 %0, %0, 0d3FF0000000000000, %1;" : "+d"(a[c]) : "d"(b));
+        else if constexpr (FORM == 1)
+          asm volatile("fma.rn.f64 %0, %0, %2, %1;" : "+d"(a[c]) : "d"(b), "d"(one));
+        else if constexpr (FORM == 4)
+          asm volatile("fma.rn.f64 %0, %0, %2, %1;" : "+d"(a[c]) : "d"(b), "d"(c_probe_one));
+        else if constexpr (FORM == 2)
+          asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(a[c]) : "d"(b));
+        else
+          asm volatile("mul.rn.f64 %0, %0, %1;" : "+d"(a[c]) : "d"(one));
+      }
     }
   }
   double s = 0.0;
@@ -49,8 +66,14 @@ __global__ void __launch_bounds__(kProbeThreads) k_fp64_fma_rate(int iters, doub
 }
 
 template <int CH>
-cudaError_t run(int iters, int ctas, cudaStream_t st) {
-  k_fp64_fma_rate<CH><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300);
+cudaError_t run(int form, int iters, int ctas, cudaStream_t st) {
+  switch (form) {
+    case 0: k_fp64_rate<CH, 0><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
+    case 1: k_fp64_rate<CH, 1><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
+    case 2: k_fp64_rate<CH, 2><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
+    case 4: k_fp64_rate<CH, 4><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
+    default: k_fp64_rate<CH, 3><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
+  }
   return cudaGetLastError();
 }
 
@@ -61,9 +84,10 @@ jacobi_status fail(jacobi_status s, const std::string& msg) {
 
 }  // namespace
 
-extern "C" jacobi_status jacobi_probe_fp64_rate(int chains, int ctas_per_sm, int64_t iters, double* lane_ops_per_s,
-                                                void* cuda_stream) {
+extern "C" jacobi_status jacobi_probe_fp64_rate(int form, int chains, int ctas_per_sm, int64_t iters,
+                                                double* lane_ops_per_s, void* cuda_stream) {
   if (!lane_ops_per_s) return fail(JACOBI_ERR_INVALID, "lane_ops_per_s is NULL");
+  if (form < 0 || form > 4) return fail(JACOBI_ERR_INVALID, "form must be 0, 1, 2, 3 or 4");
   if (chains != 1 && chains != 2 && chains != 4 && chains != 8)
     return fail(JACOBI_ERR_INVALID, "chains must be 1, 2, 4 or 8");
   if (ctas_per_sm < 1 || ctas_per_sm > 8) return fail(JACOBI_ERR_INVALID, "ctas_per_sm must be in [1, 8]");
@@ -81,10 +105,10 @@ extern "C" jacobi_status jacobi_probe_fp64_rate(int chains, int ctas_per_sm, int
   }
   auto launch = [&](int it) {
     switch (chains) {
-      case 1: return run<1>(it, ctas, st);
-      case 2: return run<2>(it, ctas, st);
-      case 4: return run<4>(it, ctas, st);
-      default: return run<8>(it, ctas, st);
+      case 1: return run<1>(form, it, ctas, st);
+      case 2: return run<2>(form, it, ctas, st);
+      case 4: return run<4>(form, it, ctas, st);
+      default: return run<8>(form, it, ctas, st);
     }
   };
   float ms = 0.f;

@@ -100,7 +100,7 @@ def load(path: str | None = None):
         "jacobi_last_error": (ctypes.c_char_p, [vp]),
         "jacobi_version": (ctypes.c_int, []),
         "jacobi_residual_noalloc": (ctypes.c_int, [ctypes.c_int, i64p, vp, vp, ctypes.POINTER(vp), vp, vp]),
-        "jacobi_probe_fp64_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, i64, dp, vp]),
+        "jacobi_probe_fp64_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, i64, dp, vp]),
         "jacobi_batch_create": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(Problem),
                                                 ctypes.c_int, vp]),
         "jacobi_batch_solve": (ctypes.c_int, [vp, ctypes.c_double, i64, ctypes.POINTER(Result)]),
@@ -276,11 +276,14 @@ def jacobi_residual_noalloc(ndim, dims, x_ptr, f_ptr, face_ptrs, rss_ptr, stream
     return _check(load().jacobi_residual_noalloc(int(ndim), d, x_ptr, f_ptr, fp, rss_ptr, stream), None)
 
 
-def jacobi_probe_fp64_rate(chains=8, ctas_per_sm=8, iters=4096, stream=None):
-    """FP64 lane operations per second of fma.rn.f64 (multiplier 1.0, the
-    form of every FP64 addition in the sweeps) on the current device."""
+def jacobi_probe_fp64_rate(form=0, chains=8, ctas_per_sm=8, iters=4096, stream=None):
+    """FP64 lane operations per second on the current device of one
+    instruction form (0: fma.rn.f64 with immediate multiplier 1.0; 1: with a
+    register multiplier 1.0; 2: add.rn.f64; 3: mul.rn.f64; 4: fma.rn.f64 with
+    the multiplier 1.0 in constant memory)."""
     v = ctypes.c_double()
-    _check(load().jacobi_probe_fp64_rate(int(chains), int(ctas_per_sm), int(iters), ctypes.byref(v), stream), None)
+    _check(load().jacobi_probe_fp64_rate(int(form), int(chains), int(ctas_per_sm), int(iters), ctypes.byref(v),
+                                         stream), None)
     return v.value
 
 

@@ -213,7 +213,8 @@ def test_size_limits_and_empty_inputs_rejected_without_gpu():
     assert lib.jacobi_residual_noalloc(3, d3(64, big, 8), x, None, None, x, None) == J.ERR_INVALID
     # the FP64 rate probe checks its arguments before any CUDA call
     v = ctypes.c_double()
-    assert lib.jacobi_probe_fp64_rate(3, 1, 16, ctypes.byref(v), None) == J.ERR_INVALID
-    assert lib.jacobi_probe_fp64_rate(8, 0, 16, ctypes.byref(v), None) == J.ERR_INVALID
-    assert lib.jacobi_probe_fp64_rate(8, 1, 0, ctypes.byref(v), None) == J.ERR_INVALID
-    assert lib.jacobi_probe_fp64_rate(8, 1, 16, None, None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(0, 3, 1, 16, ctypes.byref(v), None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(0, 8, 0, 16, ctypes.byref(v), None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(0, 8, 1, 0, ctypes.byref(v), None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(0, 8, 1, 16, None, None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(5, 8, 1, 16, ctypes.byref(v), None) == J.ERR_INVALID
