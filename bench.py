@@ -100,6 +100,7 @@ def parse():
     ap.add_argument("--march", type=int, default=-1, help="2D FP64 sweeps over march items (0/1)")
     ap.add_argument("--outer-split", type=int, default=-1, help="3D outer step in two passes (0/1)")
     ap.add_argument("--rows-low", type=int, default=0, help="lines per low-precision work item (0: library default)")
+    ap.add_argument("--l2pf", type=int, default=-1, help="FP64 sweeps: lines prefetched into L2 ahead (0: none)")
     ap.add_argument("--rows-f64", type=int, default=0, help="lines per FP64 work item (0: library default)")
     ap.add_argument("--server-opts", default="", help="serving: server options as key=value,key=value")
     ap.add_argument("--block", default="", help="override the workload's block shape, e.g. 512,64,64")
@@ -315,6 +316,8 @@ def time_form(p, form, sweeps, args, world, stream, sampler=None):
         opts["emu_adds"] = args.emu
     if form == "f64" and args.march >= 0:
         opts["march"] = args.march
+    if form == "f64" and args.l2pf >= 0:
+        opts["l2pf"] = args.l2pf
     if form != "f64" and args.tma >= 0:
         opts["tma"] = args.tma
     if form != "f64" and args.outer_split >= 0:

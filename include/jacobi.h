@@ -175,7 +175,9 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
  *                    over every 64-point segment of a range of lines in turn,
  *                    handing the edge pair of each line to the next segment
  *                    (one FP64 addition per line and segment fewer); the
- *                    ranges are sized so that all of them run in one wave
+ *                    ranges are sized so that all of them run in one wave;
+ *                    2: the same with four points per lane (128-point
+ *                    segments); 0: one warp per 64-point segment
  *   "emu_adds"       0 (default), 2 or 3: FP64 additions per warp step of the
  *                    FP64 sweep moved to the integer pipe (bit-identical;
  *                    slower on GB300, kept for measurement)
@@ -320,6 +322,9 @@ void jacobi_server_destroy(jacobi_server_t srv);
  *   form 2  add.rn.f64
  *   form 3  mul.rn.f64 by a register
  *   form 4  fma.rn.f64 with the multiplier 1.0 read from constant memory
+ *   form 5  form 1 with 2 independent 32-bit integer additions per FMA
+ *   form 6  form 1 with 4 independent 32-bit integer additions per FMA
+ *   (forms 5 and 6 count only the FMAs)
  * in `chains` (1, 2, 4 or 8) independent dependency chains per thread, with
  * ctas_per_sm (1..8) CTAs of 256 threads per SM, each thread issuing
  * 8 * chains * iters operations (iters in [1, 2^24]).  *lane_ops_per_s gets

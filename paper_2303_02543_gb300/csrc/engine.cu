@@ -86,6 +86,11 @@ void DevPool::release(void* p) {
 
 static int64_t round_up(int64_t v, int64_t m) { return (v + m - 1) / m * m; }
 
+// points per lane of the 2D FP64 march kernel for option "march" (1: two,
+// 2: four, 3: four with the lines staged in shared memory; see
+// launch_sweep_f64_march)
+static int march_width(int64_t march) { return march == 3 ? 5 : march == 2 ? 4 : 2; }
+
 static void layout(SolveHost& s) {
   const ProblemSpec& p = s.spec;
   const int nd = p.ndim;
@@ -346,7 +351,7 @@ void Workset::rebuild_tables() {
         for (const BlockDev& B : s->blocks) mlines += B.by;
   int mlen = 8;
   if (mlines > 0) {
-    const int64_t target = std::max(march_f64_resident_warps(ndim_, opt.halo == 0), 1);
+    const int64_t target = std::max(march_f64_resident_warps(ndim_, opt.halo == 0, march_width(opt.march)), 1);
     auto count = [&](int len) {
       int64_t c = 0;
       for (auto* s : solves_)
@@ -483,6 +488,7 @@ Tables Workset::tables() const {
   t.ctl = d_ctl_;
   t.spin_limit = (uint32_t)std::min<int64_t>(std::max<int64_t>(opt.spin_limit, 0), 0x7fffffff);
   t.poison = opt.poison_wait ? 1 : 0;
+  t.l2pf = (int)std::min<int64_t>(std::max<int64_t>(opt.l2pf, 0), 64);
   return t;
 }
 
@@ -704,7 +710,7 @@ void Workset::sweeps_f64(int64_t n, bool resid_last) {
     const int kpar = (int)(k & 1);
     prof_begin(kProfSweepF64);
     if (opt.march && ndim_ == 2 && !resid && opt.emu_adds == 0)
-      LAUNCH(launch_sweep_f64_march(t, kpar, push, cur_), "sweep f64");
+      LAUNCH(launch_sweep_f64_march(t, kpar, push, march_width(opt.march), cur_), "sweep f64");
     else LAUNCH(launch_sweep_f64(t, kpar, push, resid, true, (int)opt.emu_adds, cur_), "sweep f64");
     prof_end(kProfSweepF64);
     if (!push) {
@@ -1011,7 +1017,7 @@ static bool tune_cache_lookup(const std::string& key, int64_t& rows, int64_t& sc
     if (r >= 1 && (s == 0 || s == 1)) {
       rows = r;
       sched = s;
-      if (pm != std::string::npos) march = std::atoll(line.c_str() + pm + 9) != 0;
+      if (pm != std::string::npos) march = std::min<long long>(std::max<long long>(std::atoll(line.c_str() + pm + 9), 0), 3);
       found = true;
     }
   }
@@ -1077,7 +1083,10 @@ void Workset::autotune() {
     for (int64_t r : cand_rows) cands.push_back(Cand{r, sc, ref ? opt.march : 0});
   // FP64 march items are sized by the workset itself; rows only shapes the
   // residual sweeps then
-  if (!ref) cands.push_back(Cand{32, 0, 1});
+  if (!ref && ndim_ == 2) {
+    cands.push_back(Cand{32, 0, 1});
+    cands.push_back(Cand{32, 0, 2});
+  }
   const int sweeps = 8;
   {
     bool first = true;

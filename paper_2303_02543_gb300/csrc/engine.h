@@ -115,6 +115,7 @@ struct Options {
   int64_t tma = 0;           // inner sweeps (2D and 3D): stage lines in shared memory with bulk async copies
   int64_t march = 1;         // FP64 sweeps without a residual: one warp computes all segments of a line range
   int64_t outer_split = 1;   // 3D outer step as x += e over the layout, then the residual pass
+  int64_t l2pf = 0;          // FP64 sweeps: lines ahead brought into L2 by bulk prefetches (0: none)
 };
 
 // Outcome of one solve inside solve_all.

@@ -156,14 +156,16 @@ struct Tables {
   SchedCtl* ctl;
   uint32_t spin_limit;               // bounded dependency waits
   int poison;                        // test hook: every dependency wait runs out
+  int l2pf;                          // FP64 sweeps: lines ahead prefetched into L2 (0: none)
 };
 
 int launch_sweep_f64(const Tables& t, int kpar, bool push, bool resid, bool write, int emu, void* stream);
-// 2D FP64 sweep (no residual) over the march items
-int launch_sweep_f64_march(const Tables& t, int kpar, bool push, void* stream);
+// 2D FP64 sweep (no residual) over the march items; width = points per lane
+// (2: 64-point segments, 4: 128-point segments)
+int launch_sweep_f64_march(const Tables& t, int kpar, bool push, int width, void* stream);
 // warps of the 2D march sweep resident at once on the current device (0 on
 // error or in 3D)
-int march_f64_resident_warps(int ndim, bool push);
+int march_f64_resident_warps(int ndim, bool push, int width);
 int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, void* stream);
 // 2D inner sweep (not the first of a step) with rows staged in shared memory
 // by bulk asynchronous copies; a timed-out wait sets ctl->status bit 1.

@@ -60,6 +60,12 @@ __device__ __forceinline__ double dadd1(double a, double b, double one) {
 __device__ double g_fp64_one = 1.0;
 __device__ __forceinline__ double load_one() { return __ldg(&g_fp64_one); }
 
+// Bulk prefetch of `bytes` (a multiple of 16, 16-byte aligned) into L2 by the
+// TMA unit: one instruction per line, no registers, no completion to wait for.
+__device__ __forceinline__ void l2_prefetch(const void* p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 // The rare-case paths behind the warp votes below are out-of-line calls: the
 // compiler would otherwise compute them for every point and select afterwards,
 // an FP64 multiply (or a whole FP64 division) per point on a pipe that is the
@@ -448,7 +454,7 @@ template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, bo
           bool MARCH = false>
 __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __restrict__ blocks,
                                          const SolveDev* __restrict__ solves, int kpar, int epar,
-                                         const double* rd = nullptr, double* wr = nullptr) {
+                                         const double* rd = nullptr, double* wr = nullptr, int pf = 0) {
   constexpr bool WRITE = MODE != kModeResid && MODE != kModeOuterR;
   constexpr bool STORE_R = MODE == kModeOuter || MODE == kModeOuterR;
   const int lane = threadIdx.x & 31;
@@ -557,6 +563,15 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   for (int m = m0; m < mend; ++m) {
     const int64_t lc = G.line(m);
     const int col = G.col(m);
+    // lines pf steps ahead of the register loads into L2 (march items; within
+    // this item's lines and the ghost line after them)
+    if constexpr (MARCH) {
+      if (pf > 0 && lane == 0) {
+        const uint32_t bytes = (uint32_t)min(kSegF64, B.pitch - xs) * 8u;
+        if (m + 2 + pf <= mend) l2_prefetch(src.x + G.line(m + 2 + pf) + xs, bytes);
+        if (m + 1 + pf < mend) l2_prefetch(f + G.line(m + 1 + pf) + xs, bytes);
+      }
+    }
     // prefetch line m+2 and the aux values of line m+1
     typename Src::Raw2 nnr;
     LineAux an;
@@ -705,7 +720,7 @@ k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* 
 template <int DIM, bool PUSH>
 __global__ void __launch_bounds__(kThreads, 3)
 k_f64_march(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
-            const SolveDev* __restrict__ solves) {
+            const SolveDev* __restrict__ solves, int pf) {
   __shared__ double pairs[kWarps][2][kMarchLines];
   const int wi = threadIdx.x >> 5;
   const int w = blockIdx.x * kWarps + wi;
@@ -716,7 +731,265 @@ k_f64_march(const WorkItem* __restrict__ items, int nitems, int kpar, const Bloc
   for (int sg = 0; sg < nseg; ++sg) {
     it.seg = (int16_t)sg;
     f64_item<DIM, kModeSweep, PUSH, false, float, float, false, 0, true>(it, blocks, solves, kpar, 0,
-                                                                         pairs[wi][(sg + 1) & 1], pairs[wi][sg & 1]);
+                                                                         pairs[wi][(sg + 1) & 1], pairs[wi][sg & 1], pf);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// 2D FP64 sweep over march items, four points per lane (128-point segments).
+//
+// The same canonical arithmetic as f64_item, with the per-line work that is
+// not FP64 arithmetic (addresses, loads, shuffles, the edge lanes, the warp
+// vote of the exact division, the loop) spread over four points instead of
+// two: on GB300 that overhead, not the FP64 pipe, limited the two-point
+// march.  Lines are loaded with 32-byte vector loads.  The (W + S) pair of a
+// segment's first point comes from shared memory: for the block's first
+// segment the warp forms these edge pairs gW[m] + x[m-1][0] for all of its
+// lines up front, one line per lane (a handful of FP64 instructions per item
+// instead of a one-lane instruction per line); for later segments lane 31 of
+// the previous segment left its pair Q(m-1, xs-1) there.
+constexpr int kSegF64x4 = 128;
+
+
+__device__ __forceinline__ void ldg4d(const double* p, double (&v)[4]) {
+  asm("ld.global.nc.v4.f64 {%0,%1,%2,%3}, [%4];" : "=d"(v[0]), "=d"(v[1]), "=d"(v[2]), "=d"(v[3]) : "l"(p));
+}
+__device__ __forceinline__ void stg4d(double* p, const double (&v)[4]) {
+  asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};" ::"l"(p), "d"(v[0]), "d"(v[1]), "d"(v[2]), "d"(v[3])
+               : "memory");
+}
+// the valid leading elements of a 4-vector (all four in one store when valid)
+__device__ __forceinline__ void st4d_valid(double* p, const double (&v)[4], int nv) {
+  if (nv >= 4) {
+    stg4d(p, v);
+  } else {
+    if (nv > 0) p[0] = v[0];
+    if (nv > 1) p[1] = v[1];
+    if (nv > 2) p[2] = v[2];
+  }
+}
+
+// One 128-point segment of a march item: lines it.y0 .. it.y0 + it.n - 1.
+// STG > 0: x and f of the lines ahead are staged in shared memory by per-lane
+// 16-byte asynchronous copies, STG lines ahead (ring `stage`: STG slots of
+// 128 x then 128 f values per warp); each lane reads back only the bytes it
+// copied itself, so no warp barrier is needed.  STG = 0: register prefetch of
+// one line.
+__device__ __forceinline__ void cp_async16_g2s(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)), "l"(src)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <bool PUSH, int STG>
+__device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const BlockDev& B,
+                                               const BlockDev* __restrict__ blocks, const double* __restrict__ xsrc,
+                                               double* __restrict__ xd, const double* __restrict__ f,
+                                               const double* rd, double* wr, double one, int pf,
+                                               double* stage = nullptr) {
+  auto add = [one](double u, double v) { return dadd1(u, v, one); };
+  const int lane = threadIdx.x & 31;
+  const Geo<2> G(B, 0);
+  const int bx = B.bx;
+  const int xs = sg * kSegF64x4;
+  const int x = xs + 4 * lane;
+  const int nv = bx - x;                         // points of this lane: min(nv, 4) when nv > 0
+  const bool valid = nv > 0;
+  const bool holds_last = nv >= 1 && nv <= 4;    // the block's last point is x + nv - 1
+  const bool east_in = lane == 31 && nv > 4;     // east of point 3 is the next segment's first point
+  const int64_t gE = B.xoff + (int64_t)B.by;     // 2D: the east ghost column, one value per line
+  PushTargets T;
+  if constexpr (PUSH) push_targets<2>(T, B, blocks, 0);
+  const int m0 = it.y0, mend = m0 + it.n;
+
+  auto load4 = [&](int64_t o, double (&v)[4]) {
+    v[0] = v[1] = v[2] = v[3] = 0.0;
+    if (valid) ldg4d(xsrc + o, v);
+  };
+  auto loadf = [&](int64_t o, double (&v)[4]) {
+    v[0] = v[1] = v[2] = v[3] = 0.0;
+    if (valid) ldg4d(f + o, v);
+  };
+  // staged form: group j holds x of line j + 1 and f of line j
+  auto issue = [&](int j) {
+    if constexpr (STG > 0) {
+      if (j < mend && valid) {
+        double* d = stage + ((j - m0) % STG) * 256 + 4 * lane;
+        const double* sx = xsrc + G.line(j + 1) + x;
+        const double* sf = f + G.line(j) + x;
+        cp_async16_g2s(d, sx);
+        cp_async16_g2s(d + 2, sx + 2);
+        cp_async16_g2s(d + 128, sf);
+        cp_async16_g2s(d + 130, sf + 2);
+      }
+      cp_async_commit_group();
+    }
+  };
+  auto staged = [&](int j, double (&xv)[4], double (&fv)[4]) {
+    const double* d = stage + ((j - m0) % STG) * 256 + 4 * lane;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      xv[k] = valid ? d[k] : 0.0;
+      fv[k] = valid ? d[128 + k] : 0.0;
+    }
+  };
+  // prologue: lines m0 - 1 (p), m0 (c), m0 + 1 (n); pairs Q(m0 - 1, x_k)
+  double p[4], c[4], n[4], fc[4], Qp[4];
+  load4(G.line(m0 - 1) + x, p);
+  load4(G.line(m0) + x, c);
+  if constexpr (STG > 0) {
+#pragma unroll
+    for (int j = 0; j < STG; ++j) issue(m0 + j);
+    cp_async_wait_group<STG - 1>();
+    staged(m0, n, fc);
+  } else {
+    load4(G.line(m0 + 1) + x, n);
+    loadf(G.line(m0) + x, fc);
+  }
+  double ce = 0.0, ge = 0.0, pe = 0.0;
+  if (east_in) {
+    ce = __ldg(xsrc + G.line(m0) + x + 4);
+    pe = __ldg(xsrc + G.line(m0 - 1) + x + 4);
+  }
+  if (holds_last) ge = __ldg(xsrc + gE + m0);
+  {
+    double pn = __shfl_down_sync(FULL_MASK, p[0], 1);
+    if (east_in) pn = pe;
+    Qp[0] = add(p[1], c[0]);
+    Qp[1] = add(p[2], c[1]);
+    Qp[2] = add(p[3], c[2]);
+    Qp[3] = add(pn, c[3]);
+  }
+#pragma unroll 2
+  for (int m = m0; m < mend; ++m) {
+    const bool more = m + 1 < mend;
+    // lines pf steps ahead of the register loads into L2 (within this item's
+    // lines and the ghost line after them)
+    if (pf > 0 && lane == 0) {
+      const uint32_t bytes = (uint32_t)min(kSegF64x4, B.pitch - xs) * 8u;
+      if (m + 2 + pf <= mend) l2_prefetch(xsrc + G.line(m + 2 + pf) + xs, bytes);
+      if (m + 1 + pf < mend) l2_prefetch(f + G.line(m + 1 + pf) + xs, bytes);
+    }
+    // loads for the next line: x of line m + 2, f and the edge values of line m + 1
+    double nn[4], fn[4];
+    double cen = 0.0, gen = 0.0;
+    if constexpr (STG > 0) {
+      issue(m + STG);  // group m + STG into the slot group m has left
+    }
+    if (more) {
+      if constexpr (STG == 0) {
+        load4(G.line(m + 2) + x, nn);
+        loadf(G.line(m + 1) + x, fn);
+      }
+      if (east_in) cen = __ldg(xsrc + G.line(m + 1) + x + 4);
+      if (holds_last) gen = __ldg(xsrc + gE + m + 1);
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) nn[k] = fn[k] = 0.0;
+    }
+    // Q(m, x_k) = x[m][x_k + 1] + x[m + 1][x_k]; the block's last point takes the ghost
+    double ceast = __shfl_down_sync(FULL_MASK, c[0], 1);
+    if (east_in) ceast = ce;
+    double ck[4] = {c[1], c[2], c[3], ceast};
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      if (holds_last && k == nv - 1) ck[k] = ge;
+    double Q[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) Q[k] = add(ck[k], n[k]);
+    // (W + S) of point 0: the left lane's pair, or for lane 0 the pair in shared memory
+    double w0 = __shfl_up_sync(FULL_MASK, Qp[3], 1);
+    if (lane == 31) wr[m - m0] = Qp[3];
+    if (lane == 0) w0 = rd[m - m0];
+    double t[4];
+    t[0] = add(add(w0, Q[0]), fc[0]);
+    t[1] = add(add(Qp[0], Q[1]), fc[1]);
+    t[2] = add(add(Qp[1], Q[2]), fc[2]);
+    t[3] = add(add(Qp[2], Q[3]), fc[3]);
+    // t / 4 on the integer pipe; one warp vote for the four points
+    double o[4];
+    bool fast = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const uint64_t b = f64_bits(t[k]);
+      o[k] = quarter_bits(b);
+      fast = fast && (quarter_fast(b) || k >= nv);
+    }
+    if (!__all_sync(FULL_MASK, fast)) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (k < nv && !quarter_fast(f64_bits(t[k]))) o[k] = slow_quarter(t[k]);
+    }
+    if (valid) {
+      st4d_valid(xd + G.line(m) + x, o, nv);
+      if constexpr (PUSH) {
+        if (m == 0 && T.lo_line >= 0) st4d_valid(xd + T.lo_line + x, o, nv);
+        if (m == G.extent - 1 && T.hi_line >= 0) st4d_valid(xd + T.hi_line + x, o, nv);
+        if (x == 0 && T.w_col >= 0) xd[T.w_col + m] = o[0];
+        if (holds_last && T.e_col >= 0) {
+          double last = o[0];
+#pragma unroll
+          for (int k = 1; k < 4; ++k)
+            if (k == nv - 1) last = o[k];
+          xd[T.e_col + m] = last;
+        }
+      }
+    }
+    if constexpr (STG > 0) {
+      if (more) {
+        cp_async_wait_group<STG - 1>();  // group m + 1 has landed
+        staged(m + 1, nn, fn);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      Qp[k] = Q[k];
+      c[k] = n[k];
+      n[k] = nn[k];
+      fc[k] = fn[k];
+    }
+    ce = cen;
+    ge = gen;
+  }
+  if constexpr (STG > 0) cp_async_wait_group<0>();  // nothing may still target this warp's ring
+}
+
+constexpr int kMarchStages = 4;  // lines staged ahead by the shared-memory form of the 4-point march
+
+template <bool PUSH, int STG>
+__global__ void __launch_bounds__(kThreads, 2)
+k_f64_march4(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
+             const SolveDev* __restrict__ solves, int pf) {
+  __shared__ double pairs[kWarps][2][kMarchLines];
+  extern __shared__ __align__(16) double march_stage[];  // STG * 256 doubles per warp when STG > 0
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kWarps + wi;
+  if (w >= nitems) return;
+  const WorkItem it = items[w];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  if (!S->active) return;
+  const int par = (S->phase + kpar) & 1;
+  const double* __restrict__ xsrc = S->x[par];
+  double* __restrict__ xd = S->x[par ^ 1];
+  const double one = load_one();
+  // (W + S) pairs of the block's first column, x[m][-1] + x[m - 1][0], one
+  // line per lane, into the buffer lane 0 of segment 0 reads
+  const Geo<2> G(B, 0);
+  for (int j = lane; j < it.n; j += 32) {
+    const int m = it.y0 + j;
+    pairs[wi][1][j] = dadd1(__ldg(xsrc + B.xoff + m), __ldg(xsrc + G.line(m - 1)), one);
+  }
+  __syncwarp();
+  const int nseg = (B.bx + kSegF64x4 - 1) / kSegF64x4;
+  for (int sg = 0; sg < nseg; ++sg) {
+    f64_march4_seg<PUSH, STG>(it, sg, B, blocks, xsrc, xd, S->f, pairs[wi][(sg + 1) & 1], pairs[wi][sg & 1], one,
+                              pf, STG > 0 ? march_stage + wi * STG * 256 : nullptr);
     __syncwarp();
   }
 }
@@ -1804,24 +2077,48 @@ static int sweep_f64_dim(const Tables& t, int kpar, bool push, bool resid, bool 
   return (int)cudaGetLastError();
 }
 
-int launch_sweep_f64_march(const Tables& t, int kpar, bool push, void* stream) {
+static constexpr int march_stage_bytes() { return kWarps * kMarchStages * 256 * (int)sizeof(double); }
+
+// width: 2 (64-point segments), 4 (128-point segments, register prefetch),
+// 5 (128-point segments, lines staged in shared memory)
+int launch_sweep_f64_march(const Tables& t, int kpar, bool push, int width, void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (t.nm == 0) return 0;
   const dim3 g(grid_of(t.nm, kWarps)), b(kThreads);
   if (t.ndim != 2) return (int)cudaErrorInvalidValue;
-  if (push) k_f64_march<2, true><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves);
-  else k_f64_march<2, false><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves);
+  if (width == 5) {
+    const int sm = march_stage_bytes();
+    auto k = push ? k_f64_march4<true, kMarchStages> : k_f64_march4<false, kMarchStages>;
+    const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e != cudaSuccess) return (int)e;
+    k<<<g, b, sm, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
+  } else if (width == 4) {
+    if (push) k_f64_march4<true, 0><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
+    else k_f64_march4<false, 0><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
+  } else {
+    if (push) k_f64_march<2, true><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
+    else k_f64_march<2, false><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
+  }
   return (int)cudaGetLastError();
 }
 
-int march_f64_resident_warps(int ndim, bool push) {
+int march_f64_resident_warps(int ndim, bool push, int width) {
   int dev = 0, sms = 0, per_sm = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 0;
   if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
   if (ndim != 2) return 0;
-  const cudaError_t e =
-      push ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march<2, true>, kThreads, 0)
-           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march<2, false>, kThreads, 0);
+  cudaError_t e;
+  if (width == 5) {
+    const int sm = march_stage_bytes();
+    auto k = push ? k_f64_march4<true, kMarchStages> : k_f64_march4<false, kMarchStages>;
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, sm);
+  } else if (width == 4)
+    e = push ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march4<true, 0>, kThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march4<false, 0>, kThreads, 0);
+  else
+    e = push ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march<2, true>, kThreads, 0)
+             : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march<2, false>, kThreads, 0);
   if (e != cudaSuccess) return 0;
   return per_sm * sms * kWarps;
 }

@@ -33,7 +33,9 @@ __constant__ double c_probe_one = 1.0;
 
 // FORM 0: fma.rn.f64 with the immediate multiplier 1.0; 1: fma.rn.f64 with
 // the multiplier 1.0 in a register; 2: add.f64; 3: mul.f64 by a register;
-// 4: fma.rn.f64 with the multiplier 1.0 read from constant memory.
+// 4: fma.rn.f64 with the multiplier 1.0 read from constant memory; 5 and 6:
+// form 1 with 2 or 4 independent 32-bit integer additions after each FMA (to
+// see whether integer work competes with the FP64 pipe).
 template <int CH, int FORM>
 __global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(int iters, double seed) {
   double a[CH];
@@ -41,6 +43,9 @@ __global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(int iters, double s
   for (int c = 0; c < CH; ++c) a[c] = seed * (double)(threadIdx.x + 1 + c);
   const double b = seed * 1e-3;
   const double one = __ldg(&g_probe_one);
+  uint32_t ic[CH];
+#pragma unroll
+  for (int c = 0; c < CH; ++c) ic[c] = threadIdx.x + c;
   for (int i = 0; i < iters; ++i) {
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
@@ -50,7 +55,12 @@ __global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(int iters, double s
           asm volatile("fma.rn.f64 %0, %0, 0d3FF0000000000000, %1;" : "+d"(a[c]) : "d"(b));
         else if constexpr (FORM == 1)
           asm volatile("fma.rn.f64 %0, %0, %2, %1;" : "+d"(a[c]) : "d"(b), "d"(one));
-        else if constexpr (FORM == 4)
+        else if constexpr (FORM == 5 || FORM == 6) {
+          asm volatile("fma.rn.f64 %0, %0, %2, %1;" : "+d"(a[c]) : "d"(b), "d"(one));
+#pragma unroll
+          for (int q = 0; q < (FORM == 5 ? 2 : 4); ++q)
+            asm volatile("add.u32 %0, %0, %1;" : "+r"(ic[c]) : "r"(q + 1));
+        } else if constexpr (FORM == 4)
           asm volatile("fma.rn.f64 %0, %0, %2, %1;" : "+d"(a[c]) : "d"(b), "d"(c_probe_one));
         else if constexpr (FORM == 2)
           asm volatile("add.rn.f64 %0, %0, %1;" : "+d"(a[c]) : "d"(b));
@@ -62,7 +72,10 @@ __global__ void __launch_bounds__(kProbeThreads) k_fp64_rate(int iters, double s
   double s = 0.0;
 #pragma unroll
   for (int c = 0; c < CH; ++c) s += a[c];
-  if (s == 12345.678) g_probe_sink = s;  // practically never true
+  uint32_t is = 0;
+#pragma unroll
+  for (int c = 0; c < CH; ++c) is += ic[c];
+  if (s == 12345.678 || is == 0xFFFFFFFFu) g_probe_sink = s;  // practically never true
 }
 
 template <int CH>
@@ -72,6 +85,8 @@ cudaError_t run(int form, int iters, int ctas, cudaStream_t st) {
     case 1: k_fp64_rate<CH, 1><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
     case 2: k_fp64_rate<CH, 2><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
     case 4: k_fp64_rate<CH, 4><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
+    case 5: k_fp64_rate<CH, 5><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
+    case 6: k_fp64_rate<CH, 6><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
     default: k_fp64_rate<CH, 3><<<ctas, kProbeThreads, 0, st>>>(iters, 1e-300); break;
   }
   return cudaGetLastError();
@@ -87,7 +102,7 @@ jacobi_status fail(jacobi_status s, const std::string& msg) {
 extern "C" jacobi_status jacobi_probe_fp64_rate(int form, int chains, int ctas_per_sm, int64_t iters,
                                                 double* lane_ops_per_s, void* cuda_stream) {
   if (!lane_ops_per_s) return fail(JACOBI_ERR_INVALID, "lane_ops_per_s is NULL");
-  if (form < 0 || form > 4) return fail(JACOBI_ERR_INVALID, "form must be 0, 1, 2, 3 or 4");
+  if (form < 0 || form > 6) return fail(JACOBI_ERR_INVALID, "form must be in [0, 6]");
   if (chains != 1 && chains != 2 && chains != 4 && chains != 8)
     return fail(JACOBI_ERR_INVALID, "chains must be 1, 2, 4 or 8");
   if (ctas_per_sm < 1 || ctas_per_sm > 8) return fail(JACOBI_ERR_INVALID, "ctas_per_sm must be in [1, 8]");

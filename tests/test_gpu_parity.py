@@ -348,17 +348,29 @@ def test_integer_pipe_additions_bit_exact(emu, dims, block):
 @pytest.mark.parametrize("halo", [0, 1])
 @pytest.mark.parametrize("dims,block", [((300, 190), (300, 190)), ((1000, 300), (200, 150)), ((130, 77), (64, 32)),
                                         ((257, 700), (257, 700)), ((37, 29, 23), (16, 8, 8)),
-                                        ((200, 9, 150), (130, 9, 150)), ((65, 1), (64, 1)), ((3, 2), (1, 1))])
+                                        ((200, 9, 150), (130, 9, 150)), ((65, 1), (64, 1)), ((3, 2), (1, 1)),
+                                        # 4-point lanes: block widths 1..5 and 127..129 around a segment,
+                                        # ragged last lanes, many blocks per row
+                                        ((5, 33), (5, 11)), ((129, 40), (129, 40)), ((383, 70), (127, 70)),
+                                        ((512, 100), (128, 50)), ((7, 9), (2, 4))])
 def test_march_items_bit_exact(halo, dims, block):
     """One warp over all segments of a line range (edge pairs handed on in
-    shared memory) gives the bits of the per-segment items and of the oracle."""
+    shared memory), with two (march = 1) or four (march = 2) points per lane,
+    gives the bits of the per-segment items and of the oracle."""
     p = inputs.make_problem(dims, block, 59, boundary="uniform", source="normal", x0="uniform")
     out = {}
-    for march in (0, 1):
+    for march in (0, 1, 2, 3):
         with solver(p, march=march, halo=halo) as s:
             s.sweep(9)
             out[march] = s.field()
+    # lines prefetched into L2 ahead of the loads change no bit
+    with solver(p, march=2, halo=halo, l2pf=3) as s:
+        s.sweep(9)
+        out["pf"] = s.field()
     assert np.array_equal(out[1], out[0])
+    assert np.array_equal(out[2], out[0])
+    assert np.array_equal(out[3], out[0])
+    assert np.array_equal(out["pf"], out[0])
     assert np.array_equal(out[1], oracle.sweeps(p.dims, p.faces, p.source, p.x0, 9))
 
 

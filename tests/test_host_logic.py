@@ -217,4 +217,4 @@ def test_size_limits_and_empty_inputs_rejected_without_gpu():
     assert lib.jacobi_probe_fp64_rate(0, 8, 0, 16, ctypes.byref(v), None) == J.ERR_INVALID
     assert lib.jacobi_probe_fp64_rate(0, 8, 1, 0, ctypes.byref(v), None) == J.ERR_INVALID
     assert lib.jacobi_probe_fp64_rate(0, 8, 1, 16, None, None) == J.ERR_INVALID
-    assert lib.jacobi_probe_fp64_rate(5, 8, 1, 16, ctypes.byref(v), None) == J.ERR_INVALID
+    assert lib.jacobi_probe_fp64_rate(7, 8, 1, 16, ctypes.byref(v), None) == J.ERR_INVALID
