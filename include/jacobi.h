@@ -185,6 +185,15 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
  *                    stage the lines they read in shared memory by bulk async
  *                    copies (2D: the warp's line of e and r; 3D: its rows of
  *                    e with the rows above and below, and of r)
+ *   "tb"             2: in 2D, with the fused halo and one launch per sweep,
+ *                    the inner sweeps run two per launch (temporal blocking:
+ *                    one CTA per tile of 32 x 128 points keeps the first
+ *                    sweep's values in shared memory, e and r are read and e
+ *                    written once per two sweeps); bit-identical to single
+ *                    sweeps; 0: one sweep per launch; 1 (default): two per
+ *                    launch for FP32 corrections, one for bfloat16 (measured)
+ *   "l2pf"           2D FP64 march sweeps: lines brought into L2 by bulk
+ *                    prefetches ahead of the loads (0, default: none; 1..64)
  *   "outer_split"    1 (default): in 3D the refinement's outer step runs as
  *                    x_new = x + e over the whole block layout, then the
  *                    residual pass on x_new (fewer FP64 operations per point

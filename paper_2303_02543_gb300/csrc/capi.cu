@@ -256,6 +256,7 @@ static int64_t* option_slot(Options& o, const char* key) {
   if (!strcmp(key, "march")) return &o.march;
   if (!strcmp(key, "outer_split")) return &o.outer_split;
   if (!strcmp(key, "l2pf")) return &o.l2pf;
+  if (!strcmp(key, "tb")) return &o.tb;
   return nullptr;
 }
 
@@ -274,10 +275,11 @@ jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value) {
     require(value == 0 || value == 1, k + " must be 0 or 1");
   if (k == "march") require(value >= 0 && value <= 3, "march must be in [0, 3]");
   if (k == "l2pf") require(value >= 0 && value <= 64, "l2pf must be in [0, 64]");
+  if (k == "tb") require(value >= 0 && value <= 2, "tb must be 0, 1 or 2");
   const bool remarch = k == "march" && *p != value && ws.ndim() == 2;
   if (k == "spin_limit") require(value >= 0 && value <= 0x7fffffff, "spin_limit must be in [0, 2^31)");
   if (k == "emu_adds") require(value == 0 || value == 2 || value == 3, "emu_adds must be 0, 2 or 3");
-  const bool retable = ((k == "rows_f64" || k == "rows_low") && *p != value) || remarch;
+  const bool retable = ((k == "rows_f64" || k == "rows_low" || k == "tb") && *p != value) || remarch;
   *p = value;
   if (retable) ws.rebuild_tables();
   return JACOBI_OK;

@@ -324,7 +324,7 @@ void Workset::rebuild_tables() {
   for (void* p : table_allocs_) pool_.release(p);
   table_allocs_.clear();
   std::vector<BlockDev> blocks;
-  std::vector<WorkItem> w64, wlo, wm;
+  std::vector<WorkItem> w64, wlo, wm, wtb;
   int estage = 0;
   std::vector<CtaTask> t64, tlo;
   std::vector<FaceItem> faces;
@@ -406,6 +406,11 @@ void Workset::rebuild_tables() {
           wm.push_back(WorkItem{bi, 0, (int16_t)(e - a), a, 0});
         }
       }
+      if (refine() && ndim_ == 2) {  // tiles of the two-sweep inner kernel (option tb)
+        for (int y0 = 0; y0 < B.by; y0 += kTbTileH)
+          for (int xt = 0; xt * kTbTileW < B.bx; ++xt)
+            wtb.push_back(WorkItem{bi, (int16_t)xt, (int16_t)std::min(kTbTileH, B.by - y0), y0, 0});
+      }
       if (refine()) {
         // 3D rows narrower than a warp row share a warp (see low_item)
         const int v = low() == kLowBF16 ? kSegLow16 / 32 : kSegLow / 32;
@@ -439,6 +444,7 @@ void Workset::rebuild_tables() {
   d_w64_ = (WorkItem*)up(w64.data(), w64.size() * sizeof(WorkItem));
   d_wlo_ = (WorkItem*)up(wlo.data(), wlo.size() * sizeof(WorkItem));
   d_wm_ = (WorkItem*)up(wm.data(), wm.size() * sizeof(WorkItem));
+  d_wtb_ = (WorkItem*)up(wtb.data(), wtb.size() * sizeof(WorkItem));
   d_t64_ = (CtaTask*)up(t64.data(), t64.size() * sizeof(CtaTask));
   d_tlo_ = (CtaTask*)up(tlo.data(), tlo.size() * sizeof(CtaTask));
   d_faces_ = (FaceItem*)up(faces.data(), faces.size() * sizeof(FaceItem));
@@ -451,6 +457,7 @@ void Workset::rebuild_tables() {
   }
   n64_ = (int)w64.size();
   nm_ = (int)wm.size();
+  ntb_ = (int)wtb.size();
   estage_ = estage;
   nlo_ = (int)wlo.size();
   nt64_ = (int)t64.size();
@@ -469,6 +476,8 @@ Tables Workset::tables() const {
   t.n64 = n64_;
   t.wm = d_wm_;
   t.nm = nm_;
+  t.wtb = d_wtb_;
+  t.ntb = ntb_;
   t.wlo = d_wlo_;
   t.nlo = nlo_;
   t.faces = d_faces_;
@@ -762,11 +771,46 @@ void Workset::refine_outer() {
   phase_advance(1, 1);
 }
 
+bool Workset::use_tb2() const {
+  const bool want = opt.tb == 2 || (opt.tb == 1 && low() == kLowF32);
+  return want && ndim_ == 2 && opt.halo == 0 && opt.schedule == 0 && !opt.tma;
+}
+
+int Workset::inner_final_par(int64_t k) const {
+  if (k <= 0) return epar_last_;
+  if (!use_tb2()) return (int)((k - 1) & 1);
+  // an odd k starts with one sweep into e[0]; the pairs then alternate from
+  // the other buffer, and an even k starts with a pair into e[0]
+  const int64_t pairs = k / 2;
+  return (k & 1) ? (int)(pairs & 1) : (int)((pairs - 1) & 1);
+}
+
 void Workset::refine_inner(int64_t k) {
   if (tables_dirty_) rebuild_tables();
   if (k <= 0) return;
   const Tables t = tables();
   const bool push = opt.halo == 0;
+  if (use_tb2()) {
+    // two sweeps per launch: bit-identical to k single sweeps
+    int cur = -1;  // buffer holding the current correction (none: e = 0)
+    int64_t j = 0;
+    if (k & 1) {
+      prof_begin(kProfSweepLow);
+      LAUNCH(launch_sweep_low(t, 0, true, push, low(), r_bf16_, cur_), "sweep low");
+      prof_end(kProfSweepLow);
+      cur = 0;
+      j = 1;
+    }
+    for (; j < k; j += 2) {
+      const int out = cur < 0 ? 0 : cur ^ 1;
+      prof_begin(kProfSweepLow);
+      LAUNCH(launch_sweep_low_tb2(t, out ^ 1, out, cur < 0, push, low(), r_bf16_, cur_), "sweep low (two per launch)");
+      prof_end(kProfSweepLow);
+      cur = out;
+    }
+    epar_last_ = cur;
+    return;
+  }
   if (opt.schedule == 1 && push) {
     if (k > 4096) throw JErr{1, "refine_period above 4096 with the persistent scheduler"};
     sched_reset();
@@ -859,7 +903,7 @@ void Workset::step_refine(int64_t k) {
   };
   if (opt.graph && !opt.profile) {
     if (!run_graph(2 * k, body)) {
-      epar_last_ = (int)((k - 1) & 1);
+      epar_last_ = inner_final_par(k);
       for (auto* s : solves_)
         if (s && s->active) {
           s->phase ^= 1;
@@ -999,7 +1043,7 @@ static std::string tune_key(const Workset& w, const std::vector<SolveHost*>& sol
   return s;
 }
 
-static bool tune_cache_lookup(const std::string& key, int64_t& rows, int64_t& sched, int64_t& march) {
+static bool tune_cache_lookup(const std::string& key, int64_t& rows, int64_t& sched, int64_t& march, int64_t& tb) {
   const char* path = std::getenv("JACOBI_TUNE_CACHE");
   if (!path) return false;
   std::ifstream in(path);
@@ -1018,18 +1062,21 @@ static bool tune_cache_lookup(const std::string& key, int64_t& rows, int64_t& sc
       rows = r;
       sched = s;
       if (pm != std::string::npos) march = std::min<long long>(std::max<long long>(std::atoll(line.c_str() + pm + 9), 0), 3);
+      const size_t pt = line.find("\"tb\": ");
+      if (pt != std::string::npos) tb = std::min<long long>(std::max<long long>(std::atoll(line.c_str() + pt + 6), 0), 2);
       found = true;
     }
   }
   return found;
 }
 
-static void tune_cache_store(const std::string& key, int64_t rows, int64_t sched, int64_t march, double us) {
+static void tune_cache_store(const std::string& key, int64_t rows, int64_t sched, int64_t march, int64_t tb,
+                             double us) {
   const char* path = std::getenv("JACOBI_TUNE_CACHE");
   if (!path) return;
   std::ofstream out(path, std::ios::app);
   out << "{\"key\": \"" << key << "\", \"rows\": " << rows << ", \"schedule\": " << sched
-      << ", \"march\": " << march << ", \"us_per_sweep\": " << us << "}\n";
+      << ", \"march\": " << march << ", \"tb\": " << tb << ", \"us_per_sweep\": " << us << "}\n";
 }
 
 void Workset::autotune() {
@@ -1037,15 +1084,16 @@ void Workset::autotune() {
   if (live() == 0) return;
   const bool ref = refine();
   const std::string key = tune_key(*this, solves_, dtype_);
-  int64_t rows = 0, sched = 0, march = opt.march;
+  int64_t rows = 0, sched = 0, march = opt.march, tb = opt.tb;
   int64_t& opt_rows = ref ? opt.rows_low : opt.rows_f64;
-  if (tune_cache_lookup(key, rows, sched, march)) {
+  if (tune_cache_lookup(key, rows, sched, march, tb)) {
     opt_rows = rows;
     opt.schedule = sched;
     opt.march = march;
+    opt.tb = tb;
     rebuild_tables();
     tune_summary_ = "cache: rows " + std::to_string(rows) + ", schedule " + std::to_string(sched) + ", march " +
-                    std::to_string(march);
+                    std::to_string(march) + ", tb " + std::to_string(tb);
     return;
   }
   // snapshot of every FP64 iterate so the timing sweeps leave no trace
@@ -1070,22 +1118,27 @@ void Workset::autotune() {
   cuda_check(cudaEventCreate(&a), "event");
   cuda_check(cudaEventCreate(&b), "event");
   double best = 1e300;
-  int64_t best_rows = opt_rows, best_sched = opt.schedule, best_march = opt.march;
+  int64_t best_rows = opt_rows, best_sched = opt.schedule, best_march = opt.march, best_tb = opt.tb;
   // FP64 items hold whole residual groups of 8 lines; the low-precision
   // items may be shorter (small grids need many short items to fill the GPU)
   std::vector<int64_t> cand_rows = {8, 16, 32, 64, 128};
   if (ref) cand_rows.insert(cand_rows.begin(), {1, 2, 4});
   struct Cand {
-    int64_t rows, sched, march;
+    int64_t rows, sched, march, tb;
   };
   std::vector<Cand> cands;
   for (int64_t sc = 0; sc <= 1; ++sc)
-    for (int64_t r : cand_rows) cands.push_back(Cand{r, sc, ref ? opt.march : 0});
+    for (int64_t r : cand_rows) cands.push_back(Cand{r, sc, ref ? opt.march : 0, 0});
   // FP64 march items are sized by the workset itself; rows only shapes the
   // residual sweeps then
   if (!ref && ndim_ == 2) {
-    cands.push_back(Cand{32, 0, 1});
-    cands.push_back(Cand{32, 0, 2});
+    cands.push_back(Cand{32, 0, 1, 0});
+    cands.push_back(Cand{32, 0, 2, 0});
+  }
+  // 2D inner sweeps two per launch (even sweep counts time the pairs)
+  if (ref && ndim_ == 2 && opt.halo == 0) {
+    for (auto& c : cands) c.tb = 0;  // the candidates above: one sweep per launch
+    cands.push_back(Cand{16, 0, opt.march, 2});
   }
   const int sweeps = 8;
   {
@@ -1095,6 +1148,7 @@ void Workset::autotune() {
       opt_rows = r;
       opt.schedule = sc;
       opt.march = cd.march;
+      opt.tb = cd.tb;
       rebuild_tables();
       auto run = [&]() {
         if (ref) refine_inner(sweeps);
@@ -1119,6 +1173,7 @@ void Workset::autotune() {
         best_rows = r;
         best_sched = sc;
         best_march = cd.march;
+        best_tb = cd.tb;
       }
     }
   }
@@ -1129,6 +1184,7 @@ void Workset::autotune() {
   opt_rows = best_rows;
   opt.schedule = best_sched;
   opt.march = best_march;
+  opt.tb = best_tb;
   rebuild_tables();
   // restore the iterates and phases the timing sweeps changed
   if (!ref) {
@@ -1149,9 +1205,10 @@ void Workset::autotune() {
     if (solves_[k] && solves_[k]->phase != phases[k]) ctl[k] = (solves_[k]->active ? 1 : 0) | 2;
   apply_slot_ctl(ctl);
   const double us = best * 1e3 / sweeps;
-  tune_cache_store(key, best_rows, best_sched, best_march, us);
+  tune_cache_store(key, best_rows, best_sched, best_march, best_tb, us);
   tune_summary_ = "measured: rows " + std::to_string(best_rows) + ", schedule " + std::to_string(best_sched) +
-                  ", march " + std::to_string(best_march) + ", " + std::to_string(us) + " us per sweep";
+                  ", march " + std::to_string(best_march) + ", tb " + std::to_string(best_tb) + ", " +
+                  std::to_string(us) + " us per sweep";
 }
 
 // ---------------------------------------------------------------------------

@@ -116,6 +116,8 @@ struct Options {
   int64_t march = 1;         // FP64 sweeps without a residual: one warp computes all segments of a line range
   int64_t outer_split = 1;   // 3D outer step as x += e over the layout, then the residual pass
   int64_t l2pf = 0;          // FP64 sweeps: lines ahead brought into L2 by bulk prefetches (0: none)
+  int64_t tb = 1;            // inner sweeps two per launch (temporal blocking; 2D, fused halo, launch schedule):
+                             // 2 always, 0 never, 1 (default) for FP32 corrections (measured faster) only
 };
 
 // Outcome of one solve inside solve_all.
@@ -203,6 +205,9 @@ class Workset {
   void apply_slot_ctl(const std::vector<int32_t>& ctl);
   // one solve step, captured in a CUDA graph when opt.graph is set
   void step_refine(int64_t k);
+  // buffer e[.] that holds the correction after refine_inner(k)
+  int inner_final_par(int64_t k) const;
+  bool use_tb2() const;
   void chunk_f64(int64_t n);
   template <typename F>
   bool run_graph(int64_t key, F body);
@@ -231,6 +236,8 @@ class Workset {
   WorkItem* d_wlo_ = nullptr;
   WorkItem* d_wm_ = nullptr;
   int nm_ = 0;
+  WorkItem* d_wtb_ = nullptr;  // tiles of the two-sweep inner kernel
+  int ntb_ = 0;
   int estage_ = 0;  // staged 3D inner sweep: e elements per stage per warp
   // solve_all: tables hold only the active solves (retired ones dropped once
   // they are most of the tabled points); restored before solve_all returns

@@ -40,6 +40,8 @@ __host__ __device__ inline int low_lanes_log2(int bx, int v) {
   return lg;
 }
 constexpr int kMarchLines = 64;      // most lines in one FP64 march item (its shared-memory pair buffer)
+constexpr int kTbTileW = 128;        // two-sweep inner kernel: tile width (points) ...
+constexpr int kTbTileH = 32;         // ... and height (lines; measured faster than 30 or 62)
 constexpr int kRedThreads = 256;     // threads of the reduction kernel
 constexpr int kRedChunk = 4096;      // partials summed by one reduction CTA
 
@@ -144,6 +146,7 @@ struct Tables {
   const WorkItem* w64;  int n64;     // FP64 sweep / residual / refine-outer items
   const WorkItem* wlo;  int nlo;     // low-precision sweep items
   const WorkItem* wm;   int nm;      // FP64 march items (all segments of a line range)
+  const WorkItem* wtb;  int ntb;     // tiles of the two-sweep inner kernel (seg = tile column, n = lines)
   const FaceItem* faces; int nfaces; // interior faces
   const RedItem* red;   int nred;    // reduction CTAs
   const RowItem* rows;  int nrows;   // block rows
@@ -175,6 +178,11 @@ int launch_sweep_low_tma(const Tables& t, int epar, bool push, int low, bool r_b
 // elements of e per stage per warp (the largest (R + 2) * L * V over the
 // workset's blocks).
 int launch_sweep_low_stage3(const Tables& t, int epar, bool push, int low, bool r_bf16, int estage, void* stream);
+// Two inner sweeps in one launch (2D), one CTA per tile of t.wtb:
+// e[out_par] = J(J(e[in_par])), or J(J(0)) when first; bit-identical to two
+// launch_sweep_low calls.  The input buffer is not written (in_par != out_par).
+int launch_sweep_low_tb2(const Tables& t, int in_par, int out_par, bool first, bool push, int low, bool r_bf16,
+                         void* stream);
 int launch_refine_outer(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream);
 // The outer step in two passes: x[phase^1] = x[phase] + e over every element
 // of the layout (ghosts included: e's ghosts hold the neighbours' values and

@@ -819,7 +819,7 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
   auto issue = [&](int j) {
     if constexpr (STG > 0) {
       if (j < mend && valid) {
-        double* d = stage + ((j - m0) % STG) * 256 + 4 * lane;
+        double* d = stage + ((j - m0) % (STG > 0 ? STG : 1)) * 256 + 4 * lane;
         const double* sx = xsrc + G.line(j + 1) + x;
         const double* sf = f + G.line(j) + x;
         cp_async16_g2s(d, sx);
@@ -831,7 +831,7 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
     }
   };
   auto staged = [&](int j, double (&xv)[4], double (&fv)[4]) {
-    const double* d = stage + ((j - m0) % STG) * 256 + 4 * lane;
+    const double* d = stage + ((j - m0) % (STG > 0 ? STG : 1)) * 256 + 4 * lane;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       xv[k] = valid ? d[k] : 0.0;
@@ -1283,6 +1283,375 @@ k_low_free(const WorkItem* __restrict__ items, int nitems, const BlockDev* __res
   const WorkItem it = items[w];
   if (!solves[blocks[it.block].solve].active) return;
   low_item<DIM, FIRST, PUSH, TE, TR, false>(it, blocks, solves, epar);
+}
+
+// ---------------------------------------------------------------------------
+// Two inner sweeps in one pass (temporal blocking, 2D): e2 = J(J(e0)) with
+// J(e)_p = (((W + S) + (E + N)) + r_p) / 4, the arithmetic of low_item.  The
+// intermediate e1 never leaves shared memory and is rounded to the storage
+// type TE exactly as a stored e1 would be, so the result is bit-identical to
+// two separate sweeps; e0 and r are read once and e2 written once, against
+// twice each for two sweeps.
+//
+// One CTA per tile of kTbTH lines x kTbTW points of one block:
+//   1. e0 on the tile and a two-point ring, r on the tile and a one-point
+//      ring, into shared memory (as float).  Ring points outside the block
+//      are read where they live: the neighbour block's second row or column,
+//      its r, the corners of its ghost rows (so the layout needs no deeper
+//      ghost ring).  Ring points no later step reads are left 0.
+//   2. e1 on the tile and its one-point ring (0 on a domain face: the zero
+//      Dirichlet values of the correction).
+//   3. e2 on the tile, stored with the same halo push as low_item.
+// FIRST: e0 = 0, so e1 = (0 + r) / 4 and e0 is not read.  The input buffer is
+// never written: e2 and its push go to the other buffer.
+constexpr int kTbTW = kTbTileW;       // points per tile along x (4 per lane)
+constexpr int kTbTH = kTbTileH;       // lines per tile
+constexpr int kTbSP = kTbTW + 8;      // shared row stride: x = xs - 4 .. xs + kTbTW + 3, xs at index 4
+
+// one (or, persistent, two) buffers of e0 and r, one of e1
+template <typename TE, typename TR, bool PERSIST>
+__host__ __device__ constexpr int tb2_smem_bytes() {
+  return ((PERSIST ? 2 : 1) * ((kTbTH + 4) * (int)sizeof(TE) + (kTbTH + 2) * (int)sizeof(TR)) + (kTbTH + 2) * 4) *
+         kTbSP;
+}
+
+// e1 = RN_TE(v), as stored and read back by a separate sweep
+template <typename TE>
+__device__ __forceinline__ float round_store(float v) {
+  if constexpr (sizeof(TE) == 2) return __bfloat162float(__float2bfloat16_rn(v));
+  else return v;
+}
+
+// e0 at (x, y) of block B's neighbourhood, x in [-2, bx + 1], y in [-2, by + 1]
+template <typename TE>
+__device__ float tb_e0(const TE* __restrict__ es, const BlockDev* __restrict__ blocks, const BlockDev& B, int x,
+                       int y) {
+  const int bx = B.bx, by = B.by;
+  if (x >= 0 && x < bx) {
+    if (y >= -1 && y <= by) return ldf<false>(es + B.off + (int64_t)(y + 1) * B.pitch + x);
+    if (y == -2 && B.nbr[2] >= 0) {
+      const BlockDev& Sb = blocks[B.nbr[2]];
+      return ldf<false>(es + Sb.off + (int64_t)(Sb.by - 1) * Sb.pitch + x);  // S's line by_S - 2
+    }
+    if (y == by + 1 && B.nbr[3] >= 0) {
+      const BlockDev& Nb = blocks[B.nbr[3]];
+      return ldf<false>(es + Nb.off + 2 * (int64_t)Nb.pitch + x);  // N's line 1
+    }
+    return 0.f;
+  }
+  if (y < -1 || y > by) return 0.f;
+  if (x == -1) {
+    if (y >= 0 && y < by) return ldf<false>(es + B.xoff + y);  // the west ghost column
+    if (B.nbr[0] < 0) return 0.f;
+    const BlockDev& W = blocks[B.nbr[0]];
+    return ldf<false>(es + W.off + (int64_t)(y + 1) * W.pitch + W.bx - 1);  // corner of W's ghost row
+  }
+  if (x == bx) {
+    if (y >= 0 && y < by) return ldf<false>(es + B.xoff + by + y);  // the east ghost column
+    if (B.nbr[1] < 0) return 0.f;
+    const BlockDev& E = blocks[B.nbr[1]];
+    return ldf<false>(es + E.off + (int64_t)(y + 1) * E.pitch);  // corner of E's ghost row
+  }
+  if (y < 0 || y >= by) return 0.f;  // (x = -2 or bx + 1) beside a ghost row: never read
+  if (x == -2 && B.nbr[0] >= 0) {
+    const BlockDev& W = blocks[B.nbr[0]];
+    return W.bx >= 2 ? ldf<false>(es + W.off + (int64_t)(y + 1) * W.pitch + W.bx - 2) : ldf<false>(es + W.xoff + y);
+  }
+  if (x == bx + 1 && B.nbr[1] >= 0) {
+    const BlockDev& E = blocks[B.nbr[1]];
+    return E.bx >= 2 ? ldf<false>(es + E.off + (int64_t)(y + 1) * E.pitch + 1)
+                     : ldf<false>(es + E.xoff + E.by + y);
+  }
+  return 0.f;
+}
+
+// r at (x, y), x in [-1, bx], y in [-1, by] (0 at the ring's corners, never read)
+template <typename TR>
+__device__ float tb_r(const TR* __restrict__ rr, const BlockDev* __restrict__ blocks, const BlockDev& B, int x, int y) {
+  const int bx = B.bx, by = B.by;
+  if (x >= 0 && x < bx) {
+    if (y >= 0 && y < by) return ldf<false>(rr + B.off + (int64_t)(y + 1) * B.pitch + x);
+    if (y == -1 && B.nbr[2] >= 0) {
+      const BlockDev& Sb = blocks[B.nbr[2]];
+      return ldf<false>(rr + Sb.off + (int64_t)Sb.by * Sb.pitch + x);  // S's line by_S - 1
+    }
+    if (y == by && B.nbr[3] >= 0) {
+      const BlockDev& Nb = blocks[B.nbr[3]];
+      return ldf<false>(rr + Nb.off + (int64_t)Nb.pitch + x);  // N's line 0
+    }
+    return 0.f;
+  }
+  if (y < 0 || y >= by) return 0.f;
+  if (x == -1 && B.nbr[0] >= 0) {
+    const BlockDev& W = blocks[B.nbr[0]];
+    return ldf<false>(rr + W.off + (int64_t)(y + 1) * W.pitch + W.bx - 1);
+  }
+  if (x == bx && B.nbr[1] >= 0) {
+    const BlockDev& E = blocks[B.nbr[1]];
+    return ldf<false>(rr + E.off + (int64_t)(y + 1) * E.pitch);
+  }
+  return 0.f;
+}
+
+// 4 values of a line, x .. x + 3 (vector load; float or bfloat16)
+template <typename T>
+__device__ __forceinline__ void tb_ld4(const T* p, float (&v)[4]) {
+  ldv<false, 4>(p, v);
+}
+
+// V values of a lane from shared memory as float (float: 16-byte aligned
+// vector reads; bfloat16: 8- or 16-byte aligned)
+template <int V>
+__device__ __forceinline__ void unpack_smem(const float* p, float (&o)[V]) {
+#pragma unroll
+  for (int q = 0; q < V / 4; ++q) {
+    const float4 a = *reinterpret_cast<const float4*>(p + 4 * q);
+    o[4 * q] = a.x; o[4 * q + 1] = a.y; o[4 * q + 2] = a.z; o[4 * q + 3] = a.w;
+  }
+}
+template <int V>
+__device__ __forceinline__ void unpack_smem(const __nv_bfloat16* p, float (&o)[V]) {
+  if constexpr (V == 4) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    o[0] = __uint_as_float(u.x << 16); o[1] = __uint_as_float(u.x & 0xFFFF0000u);
+    o[2] = __uint_as_float(u.y << 16); o[3] = __uint_as_float(u.y & 0xFFFF0000u);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V / 8; ++q) {
+      const uint4 u = *reinterpret_cast<const uint4*>(p + 8 * q);
+      const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        o[8 * q + 2 * j] = __uint_as_float(w4[j] << 16);
+        o[8 * q + 2 * j + 1] = __uint_as_float(w4[j] & 0xFFFF0000u);
+      }
+    }
+  }
+}
+
+// cp.async of 4 or 8 bytes (cache in L1 and L2) or 16 bytes (L2 only)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_g2s(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (BYTES == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+
+// PERSIST = false (default): one CTA per tile, one buffer; the loads of a
+// tile are all in flight at once and the resident CTAs of an SM overlap one
+// another's phases.  PERSIST = true: CTAs walk the tile table (tile
+// blockIdx.x, then every gridDim.x-th) and issue the next tile's loads into
+// the other of two buffers before computing the current one (measured slower
+// at 8192^2: fewer resident CTAs, and four barriers per tile serialise them).
+template <bool PUSH, bool FIRST, typename TE, typename TR, bool PERSIST>
+__global__ void __launch_bounds__(kThreads)
+k_low_tb2(const WorkItem* __restrict__ tiles, int ntiles, const BlockDev* __restrict__ blocks,
+          const SolveDev* __restrict__ solves, int in_par, int out_par) {
+  extern __shared__ __align__(16) unsigned char tb_smem[];
+  constexpr int E0B = (kTbTH + 4) * kTbSP * (int)sizeof(TE);  // bytes of one e0 buffer
+  constexpr int RB = (kTbTH + 2) * kTbSP * (int)sizeof(TR);   // bytes of one r buffer
+  float* E1 = reinterpret_cast<float*>(tb_smem + (PERSIST ? 2 : 1) * (E0B + RB));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int xi = 4 + 4 * lane;  // shared-memory index of a lane's 4 points
+
+  // issue the loads of tile t into buffer b: line copies (asynchronous) and
+  // this thread's ring point (a plain load into `hv`, stored later at `hidx`)
+  auto issue = [&](int t, int b, float& hv, int& hidx, bool& h_is_r) {
+    hidx = -1;
+    h_is_r = false;
+    if (t < ntiles) {
+      const WorkItem tile = tiles[t];
+      const BlockDev& B = blocks[tile.block];
+      const SolveDev* S = solves + B.solve;
+      if (S->active) {
+        const TE* __restrict__ es = reinterpret_cast<const TE*>(S->e[in_par]);
+        const TR* __restrict__ rr = reinterpret_cast<const TR*>(S->r);
+        TE* E0 = reinterpret_cast<TE*>(tb_smem + b * (E0B + RB));
+        TR* R = reinterpret_cast<TR*>(tb_smem + b * (E0B + RB) + E0B);
+        const int bx = B.bx, by = B.by;
+        const int64_t pitch = B.pitch;
+        const int xs = tile.seg * kTbTW, tw = min(kTbTW, bx - xs);
+        const int y0 = tile.y0, th = tile.n;
+        const int nS = B.nbr[2], nN = B.nbr[3];
+        const int x = xs + 4 * lane;
+        if constexpr (!FIRST) {
+          for (int j = warp; j < th + 4; j += kWarps) {
+            const int y = y0 - 2 + j;
+            int64_t base = -1;
+            if (y >= -1 && y <= by) base = B.off + (int64_t)(y + 1) * pitch;
+            else if (y == -2 && nS >= 0) base = blocks[nS].off + (int64_t)(blocks[nS].by - 1) * pitch;
+            else if (y == by + 1 && nN >= 0) base = blocks[nN].off + 2 * pitch;
+            TE* d = E0 + j * kTbSP + xi;
+            if (base >= 0 && x < xs + tw) {
+              cp_async_g2s<4 * (int)sizeof(TE)>(d, es + base + x);
+            } else {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) d[k] = from_f<TE>(0.f);
+            }
+          }
+        }
+        for (int j = warp; j < th + 2; j += kWarps) {
+          const int y = y0 - 1 + j;
+          int64_t base = -1;
+          if (y >= 0 && y < by) base = B.off + (int64_t)(y + 1) * pitch;
+          else if (y == -1 && nS >= 0) base = blocks[nS].off + (int64_t)blocks[nS].by * pitch;
+          else if (y == by && nN >= 0) base = blocks[nN].off + pitch;
+          TR* d = R + j * kTbSP + xi;
+          if (base >= 0 && x < xs + tw) {
+            cp_async_g2s<4 * (int)sizeof(TR)>(d, rr + base + x);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = from_f<TR>(0.f);
+          }
+        }
+        // ring points: (th + 4) lines x 4 of e0, then (th + 2) lines x 2 of r
+        const int ne = FIRST ? 0 : (th + 4) * 4, nr = (th + 2) * 2;
+        const int q = threadIdx.x;
+        if (q < ne) {
+          const int j = q >> 2, h = q & 3;
+          const int hx = h < 2 ? xs - 2 + h : xs + tw + h - 2;
+          hv = tb_e0(es, blocks, B, hx, y0 - 2 + j);
+          hidx = j * kTbSP + hx - xs + 4;
+        } else if (q < ne + nr) {
+          const int j = (q - ne) >> 1, h = (q - ne) & 1;
+          const int hx = h == 0 ? xs - 1 : xs + tw;
+          hv = tb_r(rr, blocks, B, hx, y0 - 1 + j);
+          hidx = j * kTbSP + hx - xs + 4;
+          h_is_r = true;
+        }
+      }
+    }
+    cp_async_commit_group();
+  };
+
+  int t = blockIdx.x;
+  float hv = 0.f;
+  int hidx = -1;
+  bool h_is_r = false;
+  issue(t, 0, hv, hidx, h_is_r);
+  for (int it = 0; t < ntiles; ++it, t += gridDim.x) {
+    const int b = PERSIST ? (it & 1) : 0;
+    // loads of the next tile into the other buffer, then wait for this one's
+    float hv_n = 0.f;
+    int hidx_n = -1;
+    bool h_is_r_n = false;
+    if constexpr (PERSIST) {
+      issue(t + gridDim.x, b ^ 1, hv_n, hidx_n, h_is_r_n);
+      cp_async_wait_group<1>();
+    } else {
+      cp_async_wait_group<0>();
+    }
+    __syncthreads();  // this tile's line copies have landed: its ring points go on top
+    const WorkItem tile = tiles[t];
+    const BlockDev& B = blocks[tile.block];
+    const SolveDev* S = solves + B.solve;
+    const bool active = S->active != 0;
+    TE* E0 = reinterpret_cast<TE*>(tb_smem + b * (E0B + RB));
+    TR* R = reinterpret_cast<TR*>(tb_smem + b * (E0B + RB) + E0B);
+    if (hidx >= 0) {
+      if (h_is_r) R[hidx] = from_f<TR>(hv);
+      else E0[hidx] = from_f<TE>(hv);
+    }
+    __syncthreads();
+    const int bx = B.bx, by = B.by;
+    const int64_t pitch = B.pitch;
+    const int xs = tile.seg * kTbTW, tw = min(kTbTW, bx - xs);
+    const int y0 = tile.y0, th = tile.n;
+    const int nW = B.nbr[0], nE = B.nbr[1], nS = B.nbr[2], nN = B.nbr[3];
+    const int x = xs + 4 * lane;
+    if (active) {
+      // 2. e1 on lines y0 - 1 .. y0 + th, points xs - 1 .. xs + tw
+      for (int j = warp; j < th + 2; j += kWarps) {
+        const int y = y0 - 1 + j;
+        const bool ylive = (y >= 0 && y < by) || (y == -1 && nS >= 0) || (y == by && nN >= 0);
+        const TE* c = E0 + (j + 1) * kTbSP;
+        const TR* r = R + j * kTbSP;
+        float* o = E1 + j * kTbSP;
+        float e1v[4] = {0.f, 0.f, 0.f, 0.f};
+        if (ylive) {
+          float rk[4];
+          unpack_smem<4>(r + xi, rk);
+          if constexpr (FIRST) {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) e1v[k] = round_store<TE>(jdivf<2>(__fadd_rn(0.0f, rk[k])));
+          } else {
+            float cv[4], sk[4], nk[4];
+            unpack_smem<4>(c + xi, cv);
+            unpack_smem<4>(c - kTbSP + xi, sk);
+            unpack_smem<4>(c + kTbSP + xi, nk);
+            const float ck[6] = {to_f(c[xi - 1]), cv[0], cv[1], cv[2], cv[3], to_f(c[xi + 4])};
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+              const float tt = __fadd_rn(__fadd_rn(__fadd_rn(ck[k], sk[k]), __fadd_rn(ck[k + 2], nk[k])), rk[k]);
+              e1v[k] = round_store<TE>(jdivf<2>(tt));
+            }
+          }
+        }
+        *reinterpret_cast<float4*>(o + xi) = make_float4(e1v[0], e1v[1], e1v[2], e1v[3]);
+        if (lane < 2) {  // the ring points x = xs - 1, xs + tw (after the vector store: they may overlap it)
+          const int hx = lane == 0 ? xs - 1 : xs + tw;
+          const int i = hx - xs + 4;
+          const bool xlive = (hx >= 0 && hx < bx) || (hx == -1 && nW >= 0) || (hx == bx && nE >= 0);
+          float v = 0.f;
+          if (ylive && xlive) {
+            float tt;
+            if constexpr (FIRST) tt = __fadd_rn(0.0f, to_f(r[i]));
+            else
+              tt = __fadd_rn(__fadd_rn(__fadd_rn(to_f(c[i - 1]), to_f(c[i - kTbSP])),
+                                       __fadd_rn(to_f(c[i + 1]), to_f(c[i + kTbSP]))),
+                             to_f(r[i]));
+            v = round_store<TE>(jdivf<2>(tt));
+          }
+          o[i] = v;
+        }
+      }
+    }
+    __syncthreads();
+    if (active) {
+      // 3. e2 on lines y0 .. y0 + th - 1
+      TE* __restrict__ ed = reinterpret_cast<TE*>(S->e[out_par]);
+      PushTargets T;
+      if constexpr (PUSH) push_targets<2>(T, B, blocks, 0);
+      const int nvalid = xs + tw - x;  // > 0 when this lane holds points
+      for (int j = warp; j < th; j += kWarps) {
+        const int y = y0 + j;
+        const float* c = E1 + (j + 1) * kTbSP;
+        const float4 cv = *reinterpret_cast<const float4*>(c + xi);
+        const float4 sv = *reinterpret_cast<const float4*>(c - kTbSP + xi);
+        const float4 nv = *reinterpret_cast<const float4*>(c + kTbSP + xi);
+        float rk[4];
+        unpack_smem<4>(R + (j + 1) * kTbSP + xi, rk);
+        const float ck[6] = {c[xi - 1], cv.x, cv.y, cv.z, cv.w, c[xi + 4]};
+        const float sk[4] = {sv.x, sv.y, sv.z, sv.w}, nk[4] = {nv.x, nv.y, nv.z, nv.w};
+        float o[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          o[k] = jdivf<2>(__fadd_rn(__fadd_rn(__fadd_rn(ck[k], sk[k]), __fadd_rn(ck[k + 2], nk[k])), rk[k]));
+        if (nvalid > 0) {
+          const int64_t lc = B.off + (int64_t)(y + 1) * pitch;
+          stv<4>(ed + lc + x, o, nvalid);
+          if constexpr (PUSH) {
+            if (y == 0 && T.lo_line >= 0) stv<4>(ed + T.lo_line + x, o, nvalid);
+            if (y == by - 1 && T.hi_line >= 0) stv<4>(ed + T.hi_line + x, o, nvalid);
+            if (x == 0 && T.w_col >= 0) ed[T.w_col + y] = from_f<TE>(o[0]);
+            if (xs + tw == bx && nvalid <= 4 && T.e_col >= 0) {
+              float last = o[0];
+#pragma unroll
+              for (int k = 1; k < 4; ++k)
+                if (k == nvalid - 1) last = o[k];
+              ed[T.e_col + y] = from_f<TE>(last);
+            }
+          }
+        }
+      }
+    }
+    if constexpr (!PERSIST) break;  // one tile per CTA
+    __syncthreads();  // buffer b and E1 are free for the tile after next
+    hv = hv_n;
+    hidx = hidx_n;
+    h_is_r = h_is_r_n;
+  }
+  cp_async_wait_group<0>();  // the last (empty) group: nothing may still target shared memory
 }
 
 // ---------------------------------------------------------------------------
@@ -2376,6 +2745,35 @@ int launch_sweep_low_tma(const Tables& t, int epar, bool push, int low, bool r_b
   if (low == kLowF32) return low_tma_typed<float, float>(t, epar, push, s);
   if (r_bf16) return low_tma_typed<__nv_bfloat16, __nv_bfloat16>(t, epar, push, s);
   return low_tma_typed<__nv_bfloat16, float>(t, epar, push, s);
+}
+
+template <typename TE, typename TR, bool PERSIST>
+static int low_tb2_typed(const Tables& t, int in_par, int out_par, bool first, bool push, cudaStream_t s) {
+  const int sm = tb2_smem_bytes<TE, TR, PERSIST>();
+  auto k = first ? (push ? k_low_tb2<true, true, TE, TR, PERSIST> : k_low_tb2<false, true, TE, TR, PERSIST>)
+                 : (push ? k_low_tb2<true, false, TE, TR, PERSIST> : k_low_tb2<false, false, TE, TR, PERSIST>);
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return (int)e;
+  int g = t.ntb;  // one CTA per tile
+  if (PERSIST) {  // as many CTAs as are resident at once
+    int dev = 0, sms = 0, per_sm = 0;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return (int)e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return (int)e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, sm)) != cudaSuccess) return (int)e;
+    g = std::max(1, std::min(t.ntb, sms * std::max(1, per_sm)));
+  }
+  k<<<g, kThreads, sm, s>>>(t.wtb, t.ntb, t.blocks, t.solves, in_par, out_par);
+  return (int)cudaGetLastError();
+}
+
+int launch_sweep_low_tb2(const Tables& t, int in_par, int out_par, bool first, bool push, int low, bool r_bf16,
+                         void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.ntb == 0) return 0;
+  if (t.ndim != 2 || in_par == out_par) return (int)cudaErrorInvalidValue;
+  if (low == kLowF32) return low_tb2_typed<float, float, false>(t, in_par, out_par, first, push, s);
+  if (r_bf16) return low_tb2_typed<__nv_bfloat16, __nv_bfloat16, false>(t, in_par, out_par, first, push, s);
+  return low_tb2_typed<__nv_bfloat16, float, false>(t, in_par, out_par, first, push, s);
 }
 
 int launch_solve_ctl(SolveDev* solves, const int32_t* ctl, int nsolves, void* stream) {

@@ -443,3 +443,43 @@ def test_refine_3d_standalone_halo_matches_oracle(split, dtype, e16, r16):
         st, sw, rel = s.solve(1e-8, 10 ** 6)
         x = s.field()
     assert st == J.OK and sw == sw_o and np.array_equal(x, x_o)
+
+
+# ---- two inner sweeps per launch (temporal blocking, 2D) ----------------------
+
+TB_CASES = [((60, 45), (32, 16), 20), ((130, 77), (64, 32), 7), ((5, 33), (1, 11), 10), ((9, 7), (3, 1), 9),
+            ((300, 70), (130, 33), 20), ((513, 9), (513, 9), 6), ((257, 40), (128, 20), 11), ((2, 2), (1, 1), 4)]
+
+
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False),
+                                           ("bf16r16_refine", True, True)])
+@pytest.mark.parametrize("dims,block,period", TB_CASES)
+def test_two_sweeps_per_launch_match_oracle_emulation(dtype, e16, r16, dims, block, period):
+    """Inner sweeps fused in pairs (the first sweep's values kept in registers,
+    neighbour blocks' rows, columns, r and ghost corners read in place): the
+    same inner-sweep count and the same field bits as the oracle's emulation
+    of single sweeps, over 1-wide and 1-tall blocks, ragged segments,
+    remainder blocks and odd refinement periods."""
+    p = inputs.make_problem(dims, block, 71, boundary="uniform", source="normal", x0="zero")
+    st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, period,
+                                             e_bf16=e16, r_bf16=r16)
+    with solver(p, dtype=dtype, refine_period=period, tb=2) as s:
+        st, sw, rel = s.solve(1e-8, 10 ** 6)
+        x = s.field()
+    assert st == J.OK and st_o == oracle.OK
+    assert sw == sw_o
+    assert np.array_equal(x, x_o)
+
+
+@pytest.mark.parametrize("graph", [0, 1])
+@pytest.mark.parametrize("dims,block", [((200, 150), (64, 48)), ((37, 90), (37, 30))])
+def test_two_sweeps_per_launch_equal_single_sweeps(graph, dims, block):
+    """jacobi_sweep over several refinement steps (a partial last step too),
+    fused pairs against one sweep per launch: identical fields."""
+    p = inputs.make_problem(dims, block, 72, boundary="uniform", source="normal", x0="uniform")
+    out = {}
+    for tb in (0, 2):
+        with solver(p, dtype="f32_refine", refine_period=12, tb=tb, graph=graph) as s:
+            s.sweep(31)
+            out[tb] = s.field()
+    assert np.array_equal(out[2], out[0])
