@@ -104,6 +104,8 @@ def parse():
     ap.add_argument("--tb", type=int, default=-1, help="2D inner sweeps two per launch (2) or one (0)")
     ap.add_argument("--rows-f64", type=int, default=0, help="lines per FP64 work item (0: library default)")
     ap.add_argument("--server-opts", default="", help="serving: server options as key=value,key=value")
+    ap.add_argument("--budget-gib", type=float, default=64.0, help="serving: HBM budget of the server arena (GiB)")
+    ap.add_argument("--grace", type=float, default=60.0, help="serving: seconds after the window before censoring")
     ap.add_argument("--block", default="", help="override the workload's block shape, e.g. 512,64,64")
     ap.add_argument("--full-f64", action="store_true",
                     help="tts3d_512: run the plain FP64 solve to 1e-8 (~11 min) instead of extrapolating it, "
@@ -685,14 +687,22 @@ def serving_leg(rate, window, cap2d, cap3d, local, server_opts=None, budget=16 <
         if a.t > now:
             time.sleep(a.t - now)
         tickets.append((srv.submit(a.problem, 1e-8, 20 * 10 ** 7), a.problem))
+    # every request is done, or the deadline has passed; then each ticket is
+    # polled once without blocking (a long solve early in the stream must not
+    # hide the later ones that finished)
     deadline = t0 + window + grace
+    while time.perf_counter() < deadline:
+        s_ = srv.stats()
+        if s_["completed"] + s_["rejected"] >= len(tickets):
+            break
+        time.sleep(0.05)
     lat, lups, censored, failed = [], 0.0, 0, 0
     for t, p in tickets:
-        left = deadline - time.perf_counter()
-        if left <= 0 or not srv.wait(t, left):
+        r = srv.poll(t, want_field=False)
+        if r is None:
             censored += 1
             continue
-        st, sw, rel, secs, _ = srv.poll(t, want_field=False)
+        st, sw, rel, secs, _ = r
         if st != J.OK:
             failed += 1
         lat.append(secs)
@@ -707,8 +717,9 @@ def serving_leg(rate, window, cap2d, cap3d, local, server_opts=None, budget=16 <
     return {"offered_rate": rate, "window_s": window, "requests": len(tickets), "completed": len(lat),
             "censored": censored, "not_ok": failed, "completed_per_s": len(lat) / wall, "p50_ms": pct(0.5),
             "p99_ms": pct(0.99), "glups": lups / wall / 1e9, "steps": stats["steps"],
+            "evictions": stats["evictions"], "resumed": stats["resumed"],
             "config": {"cap2d": cap2d, "cap3d": cap3d, "dtype": "f32_refine", "tol": 1e-8,
-                       "grace_s": grace, "server_options": sopts}}
+                       "grace_s": grace, "budget_gib": budget / (1 << 30), "server_options": sopts}}
 
 
 def run_serving(args, rank, world, local):
@@ -718,7 +729,8 @@ def run_serving(args, rank, world, local):
     for kv in filter(None, args.server_opts.split(",")):
         k, v = kv.split("=")
         sopts[k.strip()] = int(v)
-    leg = serving_leg(args.rate, args.window, args.cap2d, args.cap3d, local, sopts, budget=64 << 30)
+    leg = serving_leg(args.rate, args.window, args.cap2d, args.cap3d, local, sopts,
+                      budget=int(args.budget_gib * (1 << 30)), grace=args.grace)
     if rank == 0:
         full = args.cap2d >= 4096 and args.cap3d >= 256
         leg["config"]["note"] = ("configured sizes (2D 128^2-4096^2, 3D 32^3-256^3)" if full

@@ -275,6 +275,7 @@ typedef struct {
   int64_t bytes_in_use, budget_bytes;               /* device memory of the arena */
   int64_t steps;                                    /* refinement steps run */
   double lups;                                      /* lattice-point updates of completed solves */
+  int64_t evictions, resumed;                       /* solves evicted to host memory / admitted again */
 } jacobi_server_stats;
 
 /* Start a server: one arena of hbm_budget_bytes of device memory (allocated
@@ -291,8 +292,21 @@ jacobi_status jacobi_server_create(jacobi_server_t* out, int dtype, int64_t hbm_
                                    void* cuda_stream);
 
 /* Options "refine_period", "schedule", "graph", "halo", "rows_low", "rows_f64"
- * (meaning as for contexts); JACOBI_ERR_BUSY once any request was submitted
- * (the first jacobi_server_submit fixes them). */
+ * (meaning as for contexts), and eviction under HBM pressure (the paper's
+ * memory monitor with offload, section 3.1.1):
+ *   "evict"            1: when a queued request has waited "evict_wait_steps"
+ *                      driver steps (default 2) for arena room or a slot (the
+ *                      oldest such request first), the resident solve that has run longest
+ *                      since its admission (at least "evict_min_steps" steps,
+ *                      default 20; evicted fewer than "max_evictions" times,
+ *                      default 2; at least twice the waiting request's points)
+ *                      is moved out: its iterate is copied to host
+ *                      memory, its device state freed, and it rejoins the back
+ *                      of the queue.  On readmission it continues from that
+ *                      iterate; its field and sweep count equal those of a
+ *                      solve that was never evicted.  0 (default): off.
+ * JACOBI_ERR_BUSY once any request was submitted (the first
+ * jacobi_server_submit fixes them). */
 jacobi_status jacobi_server_set_option(jacobi_server_t srv, const char* key, int64_t value);
 
 /* Queue one solve to relative residual tol (inputs are copied; thread-safe).

@@ -406,10 +406,11 @@ void Workset::rebuild_tables() {
           wm.push_back(WorkItem{bi, 0, (int16_t)(e - a), a, 0});
         }
       }
-      if (refine() && ndim_ == 2) {  // tiles of the two-sweep inner kernel (option tb)
-        for (int y0 = 0; y0 < B.by; y0 += kTbTileH)
-          for (int xt = 0; xt * kTbTileW < B.bx; ++xt)
-            wtb.push_back(WorkItem{bi, (int16_t)xt, (int16_t)std::min(kTbTileH, B.by - y0), y0, 0});
+      if (refine()) {  // tiles of the two-sweep inner kernel (option tb); in 3D each marches through all planes
+        const int tw = ndim_ == 2 ? kTbTileW : kTb3TileW, th = ndim_ == 2 ? kTbTileH : kTb3TileH;
+        for (int y0 = 0; y0 < B.by; y0 += th)
+          for (int xt = 0; xt * tw < B.bx; ++xt)
+            wtb.push_back(WorkItem{bi, (int16_t)xt, (int16_t)std::min(th, B.by - y0), y0, 0});
       }
       if (refine()) {
         // 3D rows narrower than a warp row share a warp (see low_item)
@@ -772,8 +773,8 @@ void Workset::refine_outer() {
 }
 
 bool Workset::use_tb2() const {
-  const bool want = opt.tb == 2 || (opt.tb == 1 && low() == kLowF32);
-  return want && ndim_ == 2 && opt.halo == 0 && opt.schedule == 0 && !opt.tma;
+  const bool want = opt.tb == 2 || (opt.tb == 1 && low() == kLowF32 && ndim_ == 2);
+  return want && opt.halo == 0 && opt.schedule == 0 && !opt.tma;
 }
 
 int Workset::inner_final_par(int64_t k) const {
@@ -1136,9 +1137,9 @@ void Workset::autotune() {
     cands.push_back(Cand{32, 0, 2, 0});
   }
   // 2D inner sweeps two per launch (even sweep counts time the pairs)
-  if (ref && ndim_ == 2 && opt.halo == 0) {
+  if (ref && opt.halo == 0) {
     for (auto& c : cands) c.tb = 0;  // the candidates above: one sweep per launch
-    cands.push_back(Cand{16, 0, opt.march, 2});
+    cands.push_back(Cand{ndim_ == 2 ? 16 : 32, 0, opt.march, 2});
   }
   const int sweeps = 8;
   {

@@ -42,6 +42,8 @@ __host__ __device__ inline int low_lanes_log2(int bx, int v) {
 constexpr int kMarchLines = 64;      // most lines in one FP64 march item (its shared-memory pair buffer)
 constexpr int kTbTileW = 128;        // two-sweep inner kernel: tile width (points) ...
 constexpr int kTbTileH = 32;         // ... and height (lines; measured faster than 30 or 62)
+constexpr int kTb3TileW = 64;        // 3D two-sweep inner kernel: tile width (x points) ...
+constexpr int kTb3TileH = 16;        // ... and height (y rows); the tile marches through all planes
 constexpr int kRedThreads = 256;     // threads of the reduction kernel
 constexpr int kRedChunk = 4096;      // partials summed by one reduction CTA
 

@@ -1655,6 +1655,293 @@ k_low_tb2(const WorkItem* __restrict__ tiles, int ntiles, const BlockDev* __rest
 }
 
 // ---------------------------------------------------------------------------
+// Two inner sweeps in one pass, 3D: e2 = J(J(e0)) with J(e)_p =
+// ((((W + D) + (E + U)) + (S + N)) + r_p) / 6, the arithmetic of low_item,
+// bit-identical to two separate sweeps.  One CTA per (x, y) tile of
+// kT3W x kT3H points of one block marches along z through the block's planes
+// (and the neighbours' boundary planes): at step z it forms e1 on plane z (the
+// tile and a one-point ring) and e2 on plane z - 1.  e0 planes (two-point
+// ring) and r planes (one-point ring) arrive kT3PD steps ahead: whole lines by
+// asynchronous copies into rings of kT3NS planes in shared memory, ring points
+// one per thread by plain loads kept in registers until their plane's copies
+// have landed.  Points outside the block are read where they live
+// (tblock3.cuh); e1 is 0 on domain faces.
+}  // namespace jgb
+#include "tblock3.cuh"
+namespace jgb {
+
+constexpr int kT3W = kTb3TileW;           // x points per tile (16 threads x 4)
+constexpr int kT3H = kTb3TileH;           // y rows per tile
+constexpr int kT3SP = kT3W + 8;           // shared row stride, x = xs - 4 .. xs + kT3W + 3, xs at index 4
+constexpr int kT3NS = 5;                  // planes in the e0 and r rings
+constexpr int kT3PD = 2;                  // planes loaded ahead
+constexpr int kT3E0P = (kT3H + 4) * kT3SP;  // elements of one e0 plane (rows y0 - 2 ..)
+constexpr int kT3RP = (kT3H + 2) * kT3SP;   // elements of one r or e1 plane (rows y0 - 1 ..)
+
+template <typename TE, typename TR>
+__host__ __device__ constexpr int tb3_smem_bytes() {
+  return kT3NS * kT3E0P * (int)sizeof(TE) + kT3NS * kT3RP * (int)sizeof(TR) + 3 * kT3RP * 4;
+}
+
+template <bool PUSH, bool FIRST, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads)
+k_low_tb3(const WorkItem* __restrict__ tiles, int ntiles, const BlockDev* __restrict__ blocks,
+          const SolveDev* __restrict__ solves, int in_par, int out_par) {
+  extern __shared__ __align__(16) unsigned char tb_smem[];
+  if ((int)blockIdx.x >= ntiles) return;
+  const WorkItem tile = tiles[blockIdx.x];
+  const BlockDev& B = blocks[tile.block];
+  const SolveDev* S = solves + B.solve;
+  if (!S->active) return;
+  const TE* __restrict__ es = reinterpret_cast<const TE*>(S->e[in_par]);
+  TE* __restrict__ ed = reinterpret_cast<TE*>(S->e[out_par]);
+  const TR* __restrict__ rr = reinterpret_cast<const TR*>(S->r);
+  TE* E0 = reinterpret_cast<TE*>(tb_smem);
+  TR* R = reinterpret_cast<TR*>(tb_smem + kT3NS * kT3E0P * sizeof(TE));
+  float* E1 = reinterpret_cast<float*>(tb_smem + kT3NS * kT3E0P * sizeof(TE) + kT3NS * kT3RP * sizeof(TR));
+  const int t = threadIdx.x;
+  const int bx = B.bx, by = B.by, bz = B.bz;
+  const int xs = tile.seg * kT3W, tw = min(kT3W, bx - xs);
+  const int y0 = tile.y0, th = tile.n;
+  const int c4 = t & 15, x = xs + 4 * c4, xi = 4 + 4 * c4;  // this thread's 4-point chunk of a row
+
+  // group q (q = -2 .. bz + 1): e0 plane q (rows y0 - 2 .. y0 + th + 1) and r
+  // plane q (rows y0 - 1 .. y0 + th, q in [-1, bz]) into ring slot (q + 2) % kT3NS
+  auto issue = [&](int q) {
+    if (q <= bz + 1) {
+      const int slot = (q + 2) % kT3NS;
+      if constexpr (!FIRST) {
+        for (int w = t; w < (th + 4) * 16; w += kThreads) {
+          const int j = w >> 4, xc = xs + 4 * (w & 15);
+          TE* d = E0 + slot * kT3E0P + j * kT3SP + 4 + 4 * (w & 15);
+          const int64_t base = tb3_eline(blocks, B, y0 - 2 + j, q);
+          if (base >= 0 && xc < xs + tw) {
+            cp_async_g2s<4 * (int)sizeof(TE)>(d, es + base + xc);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = from_f<TE>(0.f);
+          }
+        }
+      }
+      if (q >= -1 && q <= bz) {
+        for (int w = t; w < (th + 2) * 16; w += kThreads) {
+          const int j = w >> 4, xc = xs + 4 * (w & 15);
+          TR* d = R + slot * kT3RP + j * kT3SP + 4 + 4 * (w & 15);
+          const int64_t base = tb3_rline(blocks, B, y0 - 1 + j, q);
+          if (base >= 0 && xc < xs + tw) {
+            cp_async_g2s<4 * (int)sizeof(TR)>(d, rr + base + xc);
+          } else {
+#pragma unroll
+            for (int k = 0; k < 4; ++k) d[k] = from_f<TR>(0.f);
+          }
+        }
+      }
+    }
+    cp_async_commit_group();
+  };
+  // this thread's ring point of group q: e0 at x = xs - 2, xs - 1, xs + tw,
+  // xs + tw + 1 of each row, then r at x = xs - 1, xs + tw
+  struct Ring {
+    float v;
+    int idx;  // element index in the e0 ring, or in the r ring (is_r), or -1
+    bool is_r;
+  };
+  auto ring_load = [&](int q) {
+    Ring g{0.f, -1, false};
+    if (q > bz + 1) return g;
+    const int slot = (q + 2) % kT3NS;
+    const int ne = FIRST ? 0 : (th + 4) * 4, nr = (q >= -1 && q <= bz) ? (th + 2) * 2 : 0;
+    if (t < ne) {
+      const int j = t >> 2, h = t & 3;
+      const int hx = h < 2 ? xs - 2 + h : xs + tw + h - 2;
+      const int y = y0 - 2 + j;
+      if (hx >= 0 && hx < bx) {
+        const int64_t base = tb3_eline(blocks, B, y, q);
+        g.v = base >= 0 ? ldf<false>(es + base + hx) : 0.f;
+      } else {
+        g.v = tb3_e0_xring(es, blocks, B, hx, y, q);
+      }
+      g.idx = slot * kT3E0P + j * kT3SP + hx - xs + 4;
+    } else if (t < ne + nr) {
+      const int j = (t - ne) >> 1, h = (t - ne) & 1;
+      const int hx = h == 0 ? xs - 1 : xs + tw;
+      const int y = y0 - 1 + j;
+      if (hx >= 0 && hx < bx) {
+        const int64_t base = tb3_rline(blocks, B, y, q);
+        g.v = base >= 0 ? ldf<false>(rr + base + hx) : 0.f;
+      } else {
+        g.v = tb3_r_xring(rr, blocks, B, hx, y, q);
+      }
+      g.idx = slot * kT3RP + j * kT3SP + hx - xs + 4;
+      g.is_r = true;
+    }
+    return g;
+  };
+  auto ring_store = [&](const Ring& g) {
+    if (g.idx < 0) return;
+    if (g.is_r) R[g.idx] = from_f<TR>(g.v);
+    else E0[g.idx] = from_f<TE>(g.v);
+  };
+  // e1 is computed at (x, y, z): inside the block, or one cell outside along
+  // one axis where that neighbour exists
+  auto live = [&](int px, int py, int pz) {
+    const int ox = px < 0 ? 0 : (px >= bx ? 1 : -1);
+    const int oy = py < 0 ? 2 : (py >= by ? 3 : -1);
+    const int oz = pz < 0 ? 4 : (pz >= bz ? 5 : -1);
+    const int nout = (ox >= 0) + (oy >= 0) + (oz >= 0);
+    if (nout == 0) return true;
+    if (nout > 1) return false;
+    const int f = ox >= 0 ? ox : (oy >= 0 ? oy : oz);
+    return B.nbr[f] >= 0;
+  };
+  // prologue: groups -2 .. kT3PD - 1; the ring points of groups -2 and -1 go
+  // on top once their copies have landed, those of the next kT3PD groups wait
+  // in registers (g0: group z + 1 at step z, g1: group z + 2)
+  static_assert(kT3PD == 2, "the ring-point register pipeline holds two groups");
+  for (int q = -2; q < kT3PD; ++q) issue(q);
+  const Ring gm2 = ring_load(-2), gm1 = ring_load(-1);
+  Ring g0 = ring_load(0), g1 = ring_load(1);
+  cp_async_wait_group<kT3PD>();
+  __syncthreads();
+  ring_store(gm2);
+  ring_store(gm1);
+  for (int z = -1; z <= bz; ++z) {
+    cp_async_wait_group<kT3PD - 1>();  // this thread's copies of group z + 1 have landed
+    __syncthreads();                    // everyone's, and step z - 1 is over
+    ring_store(g0);                     // ring points of group z + 1 on top of its lines
+    g0 = g1;
+    issue(z + 1 + kT3PD);               // into the slot of plane z - 2, free since step z - 1
+    g1 = ring_load(z + 1 + kT3PD);
+    __syncthreads();
+    // e1 on plane z: the tile's rows y0 - 1 .. y0 + th, points xs - 1 .. xs + tw
+    {
+      const TE* pc = E0 + ((z + 2) % kT3NS) * kT3E0P;
+      const TE* pd = E0 + ((z + 1) % kT3NS) * kT3E0P;
+      const TE* pu = E0 + ((z + 3) % kT3NS) * kT3E0P;
+      const TR* pr = R + ((z + 2) % kT3NS) * kT3RP;
+      float* o = E1 + ((z + 3) % 3) * kT3RP;
+      const int nmain = (th + 2) * 16, nring = (th + 2) * 2;
+      for (int w = t; w < nmain + nring; w += kThreads) {
+        if (w < nmain) {
+          const int j = w >> 4, c = w & 15, xc = xs + 4 * c, ii = 4 + 4 * c;
+          const int y = y0 - 1 + j;
+          const int nv = xs + tw - xc;  // valid points of this chunk
+          if (nv <= 0) continue;
+          float e1v[4] = {0.f, 0.f, 0.f, 0.f};
+          if (live(xc, y, z)) {  // x inside the block: only y and z decide
+            float rk[4];
+            unpack_smem<4>(pr + j * kT3SP + ii, rk);
+            if constexpr (FIRST) {
+#pragma unroll
+              for (int k = 0; k < 4; ++k) e1v[k] = round_store<TE>(jdivf<3>(__fadd_rn(0.0f, rk[k])));
+            } else {
+              const TE* rowc = pc + (j + 1) * kT3SP;
+              float cv[4], sv[4], nk[4], dv[4], uv[4];
+              unpack_smem<4>(rowc + ii, cv);
+              unpack_smem<4>(rowc - kT3SP + ii, sv);
+              unpack_smem<4>(rowc + kT3SP + ii, nk);
+              unpack_smem<4>(pd + (j + 1) * kT3SP + ii, dv);
+              unpack_smem<4>(pu + (j + 1) * kT3SP + ii, uv);
+              const float ck[6] = {to_f(rowc[ii - 1]), cv[0], cv[1], cv[2], cv[3], to_f(rowc[ii + 4])};
+#pragma unroll
+              for (int k = 0; k < 4; ++k) {
+                const float tt = __fadd_rn(
+                    __fadd_rn(__fadd_rn(__fadd_rn(ck[k], dv[k]), __fadd_rn(ck[k + 2], uv[k])), __fadd_rn(sv[k], nk[k])),
+                    rk[k]);
+                e1v[k] = round_store<TE>(jdivf<3>(tt));
+              }
+            }
+          }
+          float* d = o + j * kT3SP + ii;
+          if (nv >= 4) {
+            *reinterpret_cast<float4*>(d) = make_float4(e1v[0], e1v[1], e1v[2], e1v[3]);
+          } else {  // only the valid points: x = xs + tw is the ring's (another thread)
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+              if (k < nv) d[k] = e1v[k];
+          }
+        } else {
+          const int q2 = w - nmain, j = q2 >> 1;
+          const int hx = (q2 & 1) ? xs + tw : xs - 1;
+          const int y = y0 - 1 + j, i = hx - xs + 4;
+          float v = 0.f;
+          if (live(hx, y, z)) {
+            const float rv = to_f(pr[j * kT3SP + i]);
+            float tt;
+            if constexpr (FIRST) {
+              tt = __fadd_rn(0.0f, rv);
+            } else {
+              const TE* rowc = pc + (j + 1) * kT3SP;
+              tt = __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(to_f(rowc[i - 1]), to_f(pd[(j + 1) * kT3SP + i])),
+                                                 __fadd_rn(to_f(rowc[i + 1]), to_f(pu[(j + 1) * kT3SP + i]))),
+                                       __fadd_rn(to_f(rowc[i - kT3SP]), to_f(rowc[i + kT3SP]))),
+                             rv);
+            }
+            v = round_store<TE>(jdivf<3>(tt));
+          }
+          o[j * kT3SP + i] = v;
+        }
+      }
+    }
+    __syncthreads();
+    // e2 on plane m = z - 1
+    const int m = z - 1;
+    if (m < 0 || m >= bz) continue;
+    const float* qd = E1 + ((z + 1) % 3) * kT3RP;  // e1 plane m - 1
+    const float* qc = E1 + ((z + 2) % 3) * kT3RP;  // e1 plane m
+    const float* qu = E1 + (z % 3) * kT3RP;        // e1 plane m + 1
+    const TR* pr = R + ((z + 1) % kT3NS) * kT3RP;  // r plane m
+    for (int w = t; w < th * 16; w += kThreads) {
+      const int jj = w >> 4, c = w & 15, xc = xs + 4 * c, ii = 4 + 4 * c;
+      const int y = y0 + jj;
+      const int nv = xs + tw - xc;
+      if (nv <= 0) continue;
+      const float* rowc = qc + (jj + 1) * kT3SP;
+      const float4 cv = *reinterpret_cast<const float4*>(rowc + ii);
+      const float4 sv = *reinterpret_cast<const float4*>(rowc - kT3SP + ii);
+      const float4 nv4 = *reinterpret_cast<const float4*>(rowc + kT3SP + ii);
+      const float4 dv = *reinterpret_cast<const float4*>(qd + (jj + 1) * kT3SP + ii);
+      const float4 uv = *reinterpret_cast<const float4*>(qu + (jj + 1) * kT3SP + ii);
+      float rk[4];
+      unpack_smem<4>(pr + (jj + 1) * kT3SP + ii, rk);
+      const float ck[6] = {rowc[ii - 1], cv.x, cv.y, cv.z, cv.w, rowc[ii + 4]};
+      const float sk[4] = {sv.x, sv.y, sv.z, sv.w}, nk[4] = {nv4.x, nv4.y, nv4.z, nv4.w};
+      const float dk[4] = {dv.x, dv.y, dv.z, dv.w}, uk[4] = {uv.x, uv.y, uv.z, uv.w};
+      float o2[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        o2[k] = jdivf<3>(__fadd_rn(
+            __fadd_rn(__fadd_rn(__fadd_rn(ck[k], dk[k]), __fadd_rn(ck[k + 2], uk[k])), __fadd_rn(sk[k], nk[k])), rk[k]));
+      stv<4>(ed + b3_at(B, xc, y, m), o2, nv);
+      if constexpr (PUSH) {
+        if (m == 0 && B.nbr[4] >= 0) {
+          const BlockDev& N = blocks[B.nbr[4]];
+          stv<4>(ed + b3_at(N, xc, y, N.bz), o2, nv);
+        }
+        if (m == bz - 1 && B.nbr[5] >= 0) stv<4>(ed + b3_at(blocks[B.nbr[5]], xc, y, -1), o2, nv);
+        if (y == 0 && B.nbr[2] >= 0) {
+          const BlockDev& N = blocks[B.nbr[2]];
+          stv<4>(ed + b3_at(N, xc, N.by, m), o2, nv);
+        }
+        if (y == by - 1 && B.nbr[3] >= 0) stv<4>(ed + b3_at(blocks[B.nbr[3]], xc, -1, m), o2, nv);
+        if (xc == 0 && B.nbr[0] >= 0) {
+          const BlockDev& N = blocks[B.nbr[0]];
+          ed[N.xoff + (int64_t)N.by * N.bz + (int64_t)m * N.by + y] = from_f<TE>(o2[0]);
+        }
+        if (xs + tw == bx && nv <= 4 && B.nbr[1] >= 0) {  // this chunk holds the block's last point
+          float last = o2[0];
+#pragma unroll
+          for (int k = 1; k < 4; ++k)
+            if (k == nv - 1) last = o2[k];
+          ed[blocks[B.nbr[1]].xoff + (int64_t)m * by + y] = from_f<TE>(last);
+        }
+      }
+    }
+  }
+  cp_async_wait_group<0>();  // only empty groups can be pending; none may outlive the CTA
+}
+
+// ---------------------------------------------------------------------------
 // Inner sweep with shared-memory staging by bulk asynchronous copies (2D).
 //
 // The same arithmetic as low_item, but the lines of e and r a warp needs are
@@ -2766,11 +3053,28 @@ static int low_tb2_typed(const Tables& t, int in_par, int out_par, bool first, b
   return (int)cudaGetLastError();
 }
 
+template <typename TE, typename TR>
+static int low_tb3_typed(const Tables& t, int in_par, int out_par, bool first, bool push, cudaStream_t s) {
+  const int sm = tb3_smem_bytes<TE, TR>();
+  auto k = first ? (push ? k_low_tb3<true, true, TE, TR> : k_low_tb3<false, true, TE, TR>)
+                 : (push ? k_low_tb3<true, false, TE, TR> : k_low_tb3<false, false, TE, TR>);
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return (int)e;
+  k<<<t.ntb, kThreads, sm, s>>>(t.wtb, t.ntb, t.blocks, t.solves, in_par, out_par);
+  return (int)cudaGetLastError();
+}
+
 int launch_sweep_low_tb2(const Tables& t, int in_par, int out_par, bool first, bool push, int low, bool r_bf16,
                          void* stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (t.ntb == 0) return 0;
-  if (t.ndim != 2 || in_par == out_par) return (int)cudaErrorInvalidValue;
+  if (in_par == out_par) return (int)cudaErrorInvalidValue;
+  if (t.ndim == 3) {
+    if (low == kLowF32) return low_tb3_typed<float, float>(t, in_par, out_par, first, push, s);
+    if (r_bf16) return low_tb3_typed<__nv_bfloat16, __nv_bfloat16>(t, in_par, out_par, first, push, s);
+    return low_tb3_typed<__nv_bfloat16, float>(t, in_par, out_par, first, push, s);
+  }
+  if (t.ndim != 2) return (int)cudaErrorInvalidValue;
   if (low == kLowF32) return low_tb2_typed<float, float, false>(t, in_par, out_par, first, push, s);
   if (r_bf16) return low_tb2_typed<__nv_bfloat16, __nv_bfloat16, false>(t, in_par, out_par, first, push, s);
   return low_tb2_typed<__nv_bfloat16, float, false>(t, in_par, out_par, first, push, s);

@@ -121,6 +121,11 @@ struct Request {
   int64_t max_sweeps = 0;
   int64_t bytes = 0;
   std::chrono::steady_clock::time_point t_submit;
+  // a solve that was evicted and waits to resume: inner sweeps done so far
+  // (x0 holds its iterate) and how often it has been evicted
+  int64_t resume_sweeps = 0;
+  int evictions = 0;
+  int64_t waited_steps = 0;  // driver steps spent at the head of the queue
 };
 
 struct Active {
@@ -131,6 +136,8 @@ struct Active {
   int64_t max_sweeps = 0;
   int64_t points = 0;
   std::chrono::steady_clock::time_point t_submit;
+  int64_t steps_resident = 0;  // driver steps since this admission
+  Request req;                 // the inputs, kept on the host for a resume after an eviction
 };
 
 struct Done {
@@ -161,6 +168,12 @@ struct jacobi_server {
   std::string fatal;                    // set when the driver thread fails
   jacobi_server_stats stats;
   std::string err;
+  // eviction under HBM pressure (options "evict", "evict_min_steps",
+  // "evict_wait_steps", "max_evictions")
+  bool evict = false;
+  int64_t evict_min_steps = 20;
+  int64_t evict_wait_steps = 2;
+  int64_t max_evictions = 2;
 
   ~jacobi_server() {
     {
@@ -188,7 +201,82 @@ struct jacobi_server {
 
   void loop();
   bool step_once();
+  bool maybe_evict();
 };
+
+// Eviction (the memory monitor with offload of section 3.1.1, between
+// refinement steps).  For the oldest queued request that has waited
+// evict_wait_steps driver steps for room in the arena or a slot and still
+// does not fit, the resident solve that has run longest since its admission
+// (at least evict_min_steps steps; evicted fewer than max_evictions times; at
+// least twice the waiting request's points; of the waiting request's
+// dimensionality when it lacks a slot) is evicted: its iterate is copied to host memory
+// through the page-locked stage, its device state is freed, and it joins the
+// back of the queue with its inputs and its inner-sweep count.  When it is
+// admitted again it is a new solve whose initial field is that iterate: its
+// first step computes r of that field (the r it had when it left, bit for
+// bit) and is not counted, so its later steps, its field and its sweep count
+// equal those of a solve that never left.
+bool jacobi_server::maybe_evict() {
+  if (!evict) return false;
+  struct Waiting {
+    int d;
+    int64_t need, points, waited;
+  };
+  std::vector<Waiting> waiting;
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    for (Request& h : queue) {
+      h.waited_steps += 1;
+      const int d = h.spec.ndim - 2;
+      waiting.push_back(Waiting{d, h.bytes + h.bytes / 16 + (ws[d] ? 0 : (int64_t)(1 << 20)),
+                                h.spec.n[0] * h.spec.n[1] * h.spec.n[2], h.waited_steps});
+    }
+  }
+  const int64_t room = (int64_t)arena.size() - (int64_t)arena.in_use();
+  // the oldest request that has waited long enough and does not fit, and a
+  // resident solve to give way for it
+  for (const Waiting& h : waiting) {
+    if (h.waited < evict_wait_steps) continue;
+    const bool slot_free = (int)active[h.d].size() < max_slots;
+    if (h.need <= room && slot_free) continue;  // it fits: admission will take it
+    int vd = -1, vslot = -1;
+    int64_t best = -1;
+    for (int dd = 0; dd < 2; ++dd) {
+      if (!slot_free && dd != h.d) continue;
+      for (auto& kv : active[dd]) {
+        const Active& a = kv.second;
+        // only a solve at least twice the waiting one's size gives way (two
+        // solves of similar size never evict each other)
+        if (a.steps_resident < evict_min_steps || a.req.evictions >= max_evictions || a.points < 2 * h.points)
+          continue;
+        if (a.steps_resident > best) {
+          best = a.steps_resident;
+          vd = dd;
+          vslot = kv.first;
+        }
+      }
+    }
+    if (vd < 0) continue;
+    Workset* w = ws[vd];
+    Active& a = active[vd][vslot];
+    double* staged = stage.get((size_t)a.points);  // sized at its admission: no allocation
+    w->gather(vslot, staged, 0);
+    Request r = std::move(a.req);
+    r.x0.assign(staged, staged + a.points);
+    r.spec.x0 = r.x0.data();
+    r.resume_sweeps = a.sweeps;
+    r.evictions += 1;
+    r.waited_steps = 0;
+    w->remove_solve(vslot);
+    active[vd].erase(vslot);
+    std::lock_guard<std::mutex> lk(mu);
+    queue.push_back(std::move(r));
+    stats.evictions += 1;
+    return true;  // one eviction per driver pass
+  }
+  return false;
+}
 
 // One pass of the driver: admit, step every workset once, retire.
 bool jacobi_server::step_once() {
@@ -196,6 +284,7 @@ bool jacobi_server::step_once() {
   struct PopOnExit {
     ~PopOnExit() { nvtxRangePop(); }
   } pop_on_exit;
+  maybe_evict();
   // admission: first fit, in arrival order, within the arena
   std::vector<Request> admit;
   const bool fresh = !ws[0] && !ws[1];  // the arena holds no workset state yet
@@ -243,9 +332,19 @@ bool jacobi_server::step_once() {
       a.max_sweeps = r.max_sweeps;
       a.points = r.spec.n[0] * r.spec.n[1] * r.spec.n[2];
       a.t_submit = r.t_submit;
-      active[d][slot] = a;
+      a.sweeps = r.resume_sweeps;  // a resumed solve continues its count
+      const bool resumed = r.evictions > 0;
+      if (evict) {
+        // keep the inputs on the host for a later resume (not the initial field)
+        a.req = std::move(r);
+        a.req.x0.clear();
+        a.req.x0.shrink_to_fit();
+        a.req.spec.x0 = nullptr;
+      }
+      active[d][slot] = std::move(a);
       std::lock_guard<std::mutex> lk(mu);
       stats.admitted += 1;
+      if (resumed) stats.resumed += 1;
     } catch (const JErr& e) {
       if (e.code != JACOBI_ERR_OOM && e.code != JACOBI_ERR_BUSY) throw;
       // Out of arena (fragmentation, or workset tables larger than the margin).
@@ -293,6 +392,7 @@ bool jacobi_server::step_once() {
       Active& a = kv.second;
       if (a.had_outer) a.sweeps += k;
       a.had_outer = true;
+      a.steps_resident += 1;
       const SolveHost* s = w->solve(kv.first);
       const double rel = s->bss > 0.0 ? std::sqrt(rss[kv.first]) / std::sqrt(s->bss) : std::sqrt(rss[kv.first]);
       int st = -1;
@@ -429,6 +529,14 @@ jacobi_status jacobi_server_set_option(jacobi_server_t srv, const char* key, int
   } else if (k == "schedule" || k == "graph" || k == "halo") {
     if (value != 0 && value != 1) throw JErr{JACOBI_ERR_INVALID, k + " must be 0 or 1"};
     (k == "schedule" ? srv->opt.schedule : k == "graph" ? srv->opt.graph : srv->opt.halo) = value;
+  } else if (k == "evict") {
+    if (value != 0 && value != 1) throw JErr{JACOBI_ERR_INVALID, "evict must be 0 or 1"};
+    srv->evict = value != 0;
+  } else if (k == "evict_min_steps" || k == "evict_wait_steps" || k == "max_evictions") {
+    if (value < (k == "evict_wait_steps" ? 0 : 1) || value > (1LL << 40))
+      throw JErr{JACOBI_ERR_INVALID, k + " out of range"};
+    (k == "evict_min_steps" ? srv->evict_min_steps : k == "evict_wait_steps" ? srv->evict_wait_steps
+                                                                              : srv->max_evictions) = value;
   } else if (k == "rows_low" || k == "rows_f64") {
     if (value < (k == "rows_low" ? 0 : 1))
       throw JErr{JACOBI_ERR_INVALID, k == "rows_low" ? "rows_low must be >= 0 (0: automatic)" : "rows_f64 must be >= 1"};

@@ -51,8 +51,9 @@ class Problem(ctypes.Structure):
 
 
 class ServerStats(ctypes.Structure):
-    _fields_ = [(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "rejected", "active", "queued",
-                                              "bytes_in_use", "budget_bytes", "steps")] + [("lups", ctypes.c_double)]
+    _fields_ = ([(n, ctypes.c_int64) for n in ("submitted", "admitted", "completed", "rejected", "active", "queued",
+                                               "bytes_in_use", "budget_bytes", "steps")] + [("lups", ctypes.c_double)]
+                + [("evictions", ctypes.c_int64), ("resumed", ctypes.c_int64)])
 
 
 class Result(ctypes.Structure):

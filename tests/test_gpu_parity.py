@@ -483,3 +483,27 @@ def test_two_sweeps_per_launch_equal_single_sweeps(graph, dims, block):
             s.sweep(31)
             out[tb] = s.field()
     assert np.array_equal(out[2], out[0])
+
+
+TB3_CASES = [((40, 33, 20), (32, 11, 20), 20), ((70, 9, 8), (64, 5, 4), 7), ((16, 14, 12), (8, 7, 6), 10),
+             ((130, 20, 9), (64, 16, 9), 6), ((5, 6, 7), (1, 1, 1), 5), ((66, 40, 18), (66, 17, 5), 9)]
+
+
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False),
+                                           ("bf16r16_refine", True, True)])
+@pytest.mark.parametrize("dims,block,period", TB3_CASES)
+def test_two_sweeps_per_launch_3d_match_oracle_emulation(dtype, e16, r16, dims, block, period):
+    """3D inner sweeps fused in pairs (a CTA per (x, y) tile marching along z,
+    neighbour planes, rows, columns and the edges of their ghost rings read in
+    place): the same inner-sweep count and field bits as the oracle's
+    emulation of single sweeps, over ragged and partial tiles, 1x1x1 blocks,
+    remainder blocks and odd refinement periods."""
+    p = inputs.make_problem(dims, block, 73, boundary="uniform", source="normal", x0="zero")
+    st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, period,
+                                             e_bf16=e16, r_bf16=r16)
+    with solver(p, dtype=dtype, refine_period=period, tb=2) as s:
+        st, sw, rel = s.solve(1e-8, 10 ** 6)
+        x = s.field()
+    assert st == J.OK and st_o == oracle.OK
+    assert sw == sw_o
+    assert np.array_equal(x, x_o)

@@ -182,3 +182,55 @@ def test_options_are_fixed_by_the_first_submit():
         srv.poll(t)
         # still fixed after the queue drained and the solve retired
         assert J.load().jacobi_server_set_option(srv.h, b"refine_period", 10) == J.ERR_BUSY
+
+
+@pytest.mark.parametrize("dtype", ["f32_refine", "bf16_refine"])
+def test_evicted_solve_resumes_bit_identical(dtype):
+    """Serving under HBM pressure: with one slot, small requests that queue
+    behind a long solve make the server evict it to host memory; they run and
+    finish first, and the long solve, admitted again, returns the same field
+    and sweep count as a solve that was never evicted, bit for bit."""
+    long_ = inputs.make_problem((200, 160), (64, 64), 130, boundary="uniform", source="normal")
+    shorts = [inputs.make_problem((40, 30), (20, 30), 131 + i, boundary="uniform", source="normal") for i in range(3)]
+    with J.Server(dtype, budget_bytes=256 << 20, max_slots=1, refine_period=K, evict=1, evict_min_steps=5,
+                  evict_wait_steps=1) as srv:
+        tl = srv.submit(long_, 1e-8, MAXS)
+        while srv.stats()["steps"] < 10:
+            time.sleep(0.001)
+        ts = [srv.submit(p, 1e-8, MAXS) for p in shorts]
+        for t in ts:
+            assert srv.wait(t, 120.0)
+        rs = [srv.poll(t) for t in ts]
+        assert srv.wait(tl, 300.0)
+        rl = srv.poll(tl)
+        stats = srv.stats()
+    assert stats["evictions"] == 1 and stats["resumed"] == 1
+    assert rl[3] > max(r[3] for r in rs)  # the long solve finished last
+    for p, r in zip(shorts + [long_], rs + [rl]):
+        st1, sw1, x1 = alone(p, dtype)
+        assert r[0] == J.OK and st1 == J.OK
+        assert r[1] == sw1
+        assert np.array_equal(r[4], x1)
+
+
+def test_without_eviction_small_requests_wait_for_the_slot():
+    long_ = inputs.make_problem((200, 160), (64, 64), 130, boundary="uniform", source="normal")
+    short = inputs.make_problem((40, 30), (20, 30), 131, boundary="uniform", source="normal")
+    with J.Server("f32_refine", budget_bytes=256 << 20, max_slots=1, refine_period=K) as srv:
+        tl = srv.submit(long_, 1e-8, MAXS)
+        while srv.stats()["steps"] < 10:
+            time.sleep(0.001)
+        t = srv.submit(short, 1e-8, MAXS)
+        assert srv.wait(t, 300.0) and srv.wait(tl, 300.0)
+        rs, rl = srv.poll(t), srv.poll(tl)
+        assert srv.stats()["evictions"] == 0
+    assert rs[3] > rl[3]  # queued behind the long solve
+    assert np.array_equal(rl[4], alone(long_)[2])
+
+
+def test_eviction_options_are_checked():
+    with J.Server("f32_refine", budget_bytes=16 << 20, max_slots=2) as srv:
+        for k, v in (("evict", 2), ("evict_min_steps", 0), ("evict_wait_steps", -1), ("max_evictions", 0)):
+            with pytest.raises(J.JacobiError) as e:
+                J._check(J.load().jacobi_server_set_option(srv.h, k.encode(), v), None)
+            assert e.value.status == J.ERR_INVALID
