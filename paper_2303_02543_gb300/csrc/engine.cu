@@ -406,11 +406,13 @@ void Workset::rebuild_tables() {
           wm.push_back(WorkItem{bi, 0, (int16_t)(e - a), a, 0});
         }
       }
-      if (refine()) {  // tiles of the two-sweep inner kernel (option tb); in 3D each marches through all planes
+      if (refine()) {  // tiles of the two-sweep inner kernel (option tb); in 3D a tile spans kTb3TileZ planes
         const int tw = ndim_ == 2 ? kTbTileW : kTb3TileW, th = ndim_ == 2 ? kTbTileH : kTb3TileH;
-        for (int y0 = 0; y0 < B.by; y0 += th)
-          for (int xt = 0; xt * tw < B.bx; ++xt)
-            wtb.push_back(WorkItem{bi, (int16_t)xt, (int16_t)std::min(th, B.by - y0), y0, 0});
+        const int tz = ndim_ == 2 ? 1 : kTb3TileZ;
+        for (int z0 = 0; z0 < B.bz; z0 += tz)
+          for (int y0 = 0; y0 < B.by; y0 += th)
+            for (int xt = 0; xt * tw < B.bx; ++xt)
+              wtb.push_back(WorkItem{bi, (int16_t)xt, (int16_t)std::min(th, B.by - y0), y0, ndim_ == 2 ? 0 : z0});
       }
       if (refine()) {
         // 3D rows narrower than a warp row share a warp (see low_item)

@@ -43,7 +43,8 @@ constexpr int kMarchLines = 64;      // most lines in one FP64 march item (its s
 constexpr int kTbTileW = 128;        // two-sweep inner kernel: tile width (points) ...
 constexpr int kTbTileH = 32;         // ... and height (lines; measured faster than 30 or 62)
 constexpr int kTb3TileW = 64;        // 3D two-sweep inner kernel: tile width (x points) ...
-constexpr int kTb3TileH = 16;        // ... and height (y rows); the tile marches through all planes
+constexpr int kTb3TileH = 16;        // ... height (y rows) ...
+constexpr int kTb3TileZ = 16;        // ... and depth (z planes it marches through)
 constexpr int kRedThreads = 256;     // threads of the reduction kernel
 constexpr int kRedChunk = 4096;      // partials summed by one reduction CTA
 

@@ -1658,9 +1658,10 @@ k_low_tb2(const WorkItem* __restrict__ tiles, int ntiles, const BlockDev* __rest
 // Two inner sweeps in one pass, 3D: e2 = J(J(e0)) with J(e)_p =
 // ((((W + D) + (E + U)) + (S + N)) + r_p) / 6, the arithmetic of low_item,
 // bit-identical to two separate sweeps.  One CTA per (x, y) tile of
-// kT3W x kT3H points of one block marches along z through the block's planes
-// (and the neighbours' boundary planes): at step z it forms e1 on plane z (the
-// tile and a one-point ring) and e2 on plane z - 1.  e0 planes (two-point
+// kT3W x kT3H points and kTb3TileZ planes of one block marches along z (one
+// plane further on each side for e1, two for e0: the neighbours' boundary
+// planes at the block's faces): at step z it forms e1 on plane z (the tile and
+// a one-point ring) and e2 on plane z - 1.  e0 planes (two-point
 // ring) and r planes (one-point ring) arrive kT3PD steps ahead: whole lines by
 // asynchronous copies into rings of kT3NS planes in shared memory, ring points
 // one per thread by plain loads kept in registers until their plane's copies
@@ -1703,12 +1704,14 @@ k_low_tb3(const WorkItem* __restrict__ tiles, int ntiles, const BlockDev* __rest
   const int bx = B.bx, by = B.by, bz = B.bz;
   const int xs = tile.seg * kT3W, tw = min(kT3W, bx - xs);
   const int y0 = tile.y0, th = tile.n;
+  // this tile's planes: e2 on z0 .. z1 - 1, e1 on z0 - 1 .. z1, e0 on z0 - 2 .. z1 + 1
+  const int z0 = tile.z0, z1 = min(z0 + kTb3TileZ, bz);
   const int c4 = t & 15, x = xs + 4 * c4, xi = 4 + 4 * c4;  // this thread's 4-point chunk of a row
 
-  // group q (q = -2 .. bz + 1): e0 plane q (rows y0 - 2 .. y0 + th + 1) and r
-  // plane q (rows y0 - 1 .. y0 + th, q in [-1, bz]) into ring slot (q + 2) % kT3NS
+  // group q (q = z0 - 2 .. z1 + 1): e0 plane q (rows y0 - 2 .. y0 + th + 1) and
+  // r plane q (rows y0 - 1 .. y0 + th, q in [-1, bz]) into ring slot (q + 2) % kT3NS
   auto issue = [&](int q) {
-    if (q <= bz + 1) {
+    if (q <= z1 + 1) {
       const int slot = (q + 2) % kT3NS;
       if constexpr (!FIRST) {
         for (int w = t; w < (th + 4) * 16; w += kThreads) {
@@ -1748,7 +1751,7 @@ k_low_tb3(const WorkItem* __restrict__ tiles, int ntiles, const BlockDev* __rest
   };
   auto ring_load = [&](int q) {
     Ring g{0.f, -1, false};
-    if (q > bz + 1) return g;
+    if (q > z1 + 1) return g;
     const int slot = (q + 2) % kT3NS;
     const int ne = FIRST ? 0 : (th + 4) * 4, nr = (q >= -1 && q <= bz) ? (th + 2) * 2 : 0;
     if (t < ne) {
@@ -1798,14 +1801,14 @@ k_low_tb3(const WorkItem* __restrict__ tiles, int ntiles, const BlockDev* __rest
   // on top once their copies have landed, those of the next kT3PD groups wait
   // in registers (g0: group z + 1 at step z, g1: group z + 2)
   static_assert(kT3PD == 2, "the ring-point register pipeline holds two groups");
-  for (int q = -2; q < kT3PD; ++q) issue(q);
-  const Ring gm2 = ring_load(-2), gm1 = ring_load(-1);
-  Ring g0 = ring_load(0), g1 = ring_load(1);
+  for (int q = z0 - 2; q < z0 + kT3PD; ++q) issue(q);
+  const Ring gm2 = ring_load(z0 - 2), gm1 = ring_load(z0 - 1);
+  Ring g0 = ring_load(z0), g1 = ring_load(z0 + 1);
   cp_async_wait_group<kT3PD>();
   __syncthreads();
   ring_store(gm2);
   ring_store(gm1);
-  for (int z = -1; z <= bz; ++z) {
+  for (int z = z0 - 1; z <= z1; ++z) {
     cp_async_wait_group<kT3PD - 1>();  // this thread's copies of group z + 1 have landed
     __syncthreads();                    // everyone's, and step z - 1 is over
     ring_store(g0);                     // ring points of group z + 1 on top of its lines
@@ -1886,7 +1889,7 @@ k_low_tb3(const WorkItem* __restrict__ tiles, int ntiles, const BlockDev* __rest
     __syncthreads();
     // e2 on plane m = z - 1
     const int m = z - 1;
-    if (m < 0 || m >= bz) continue;
+    if (m < z0 || m >= z1) continue;
     const float* qd = E1 + ((z + 1) % 3) * kT3RP;  // e1 plane m - 1
     const float* qc = E1 + ((z + 2) % 3) * kT3RP;  // e1 plane m
     const float* qu = E1 + (z % 3) * kT3RP;        // e1 plane m + 1

@@ -486,7 +486,9 @@ def test_two_sweeps_per_launch_equal_single_sweeps(graph, dims, block):
 
 
 TB3_CASES = [((40, 33, 20), (32, 11, 20), 20), ((70, 9, 8), (64, 5, 4), 7), ((16, 14, 12), (8, 7, 6), 10),
-             ((130, 20, 9), (64, 16, 9), 6), ((5, 6, 7), (1, 1, 1), 5), ((66, 40, 18), (66, 17, 5), 9)]
+             ((130, 20, 9), (64, 16, 9), 6), ((5, 6, 7), (1, 1, 1), 5), ((66, 40, 18), (66, 17, 5), 9),
+             # several 16-plane chunks per block, a partial last chunk
+             ((24, 20, 40), (24, 20, 40), 8), ((30, 17, 35), (16, 17, 33), 11)]
 
 
 @pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False),
