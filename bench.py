@@ -97,7 +97,7 @@ def parse():
     ap.add_argument("--forms", default="f64,f32_refine,bf16_refine")
     ap.add_argument("--emu", type=int, default=-1, help="FP64 additions per warp step on the integer pipe (0, 2, 3)")
     ap.add_argument("--tma", type=int, default=-1, help="2D inner sweeps staged by bulk async copies (0/1)")
-    ap.add_argument("--march", type=int, default=-1, help="2D FP64 sweeps over march items (0/1)")
+    ap.add_argument("--march", type=int, default=-1, help="2D FP64 sweeps over march items (0..3; -1: the library default, 3)")
     ap.add_argument("--outer-split", type=int, default=-1, help="3D outer step in two passes (0/1)")
     ap.add_argument("--rows-low", type=int, default=0, help="lines per low-precision work item (0: library default)")
     ap.add_argument("--l2pf", type=int, default=-1, help="FP64 sweeps: lines prefetched into L2 ahead (0: none)")

@@ -171,13 +171,20 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
  *                    shapes and schedules and keep the fastest (cached in the
  *                    file named by the environment variable JACOBI_TUNE_CACHE)
  *   "profile"        1: time every kernel launch with CUDA events (see jacobi_profile)
- *   "march"          1 (default): 2D FP64 sweeps that test no residual run one warp
+ *   "march"          1: 2D FP64 sweeps that test no residual run one warp
  *                    over every 64-point segment of a range of lines in turn,
  *                    handing the edge pair of each line to the next segment
  *                    (one FP64 addition per line and segment fewer); the
  *                    ranges are sized so that all of them run in one wave;
  *                    2: the same with four points per lane (128-point
- *                    segments); 0: one warp per 64-point segment
+ *                    segments), the next line's loads issued into registers
+ *                    before the current line's arithmetic; 3 (default): four
+ *                    points per lane with the lines ahead staged in a ring
+ *                    of shared-memory buffers by per-lane async copies, and
+ *                    the 2D fused-residual sweep and refinement outer step
+ *                    also run over march items (ranges of whole residual
+ *                    groups); bit-identical to 0; 0: one warp per 64-point
+ *                    segment
  *   "emu_adds"       0 (default), 2 or 3: FP64 additions per warp step of the
  *                    FP64 sweep moved to the integer pipe (bit-identical;
  *                    slower on GB300, kept for measurement)

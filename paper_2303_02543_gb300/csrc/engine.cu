@@ -324,7 +324,7 @@ void Workset::rebuild_tables() {
   for (void* p : table_allocs_) pool_.release(p);
   table_allocs_.clear();
   std::vector<BlockDev> blocks;
-  std::vector<WorkItem> w64, wlo, wm, wtb;
+  std::vector<WorkItem> w64, wlo, wm, wmr, wtb;
   int estage = 0;
   std::vector<CtaTask> t64, tlo;
   std::vector<FaceItem> faces;
@@ -350,7 +350,7 @@ void Workset::rebuild_tables() {
       if (s)
         for (const BlockDev& B : s->blocks) mlines += B.by;
   int mlen = 8;
-  if (mlines > 0) {
+  if (mlines > 0 && opt.march != 3) {
     const int64_t target = std::max(march_f64_resident_warps(ndim_, opt.halo == 0, march_width(opt.march)), 1);
     auto count = [&](int len) {
       int64_t c = 0;
@@ -362,6 +362,8 @@ void Workset::rebuild_tables() {
     mlen = (int)std::min<int64_t>(std::max<int64_t>((mlines + target - 1) / target, 8), kMarchLines);
     while (mlen < kMarchLines && count(mlen) > target) ++mlen;
   }
+  // option march 3: the blocks whose lines the march kernels deal out
+  std::vector<std::pair<int, int>> mblk;  // (block index, lines)
   tabled_points_ = 0;
   for (int slot = 0; slot < capacity_; ++slot) {
     SolveHost* s = solves_[slot];
@@ -399,7 +401,9 @@ void Workset::rebuild_tables() {
         return nt;
       };
       B.nt64 = items(w64, t64, kSegF64, r64, 1);
-      if (ndim_ == 2) {
+      if (ndim_ == 2 && opt.march == 3) {
+        mblk.emplace_back(bi, ext);  // dealt out in runs below
+      } else if (ndim_ == 2) {
         const int pieces = (ext + mlen - 1) / mlen;
         for (int q = 0; q < pieces; ++q) {
           const int a = (int)((int64_t)ext * q / pieces), e = (int)((int64_t)ext * (q + 1) / pieces);
@@ -436,6 +440,44 @@ void Workset::rebuild_tables() {
       red.push_back(RedItem{slot, c, s->nchunks, (int)std::min<int64_t>(kRedChunk, s->nparts - start), start});
     }
   }
+  // option march 3: the lines of all blocks, in block order, dealt out in
+  // equal runs, one per warp (as many warps as the kernel keeps resident, but
+  // runs of at least 8 lines, and more warps only where a run would exceed
+  // kMarchLines); a run crossing a block boundary becomes two items.  `unit` lines per step: 1 for the plain
+  // sweep, kResGroup for the fused-residual sweep and the outer step, whose
+  // items must hold whole residual groups.
+  std::vector<int> wms, wmrs;
+  auto deal = [&](int64_t target, int unit, std::vector<WorkItem>& out, std::vector<int>& start) {
+    int64_t total = 0;
+    for (const auto& mb : mblk) total += (mb.second + unit - 1) / unit;
+    if (total == 0) return;
+    const int64_t wmax = kMarchLines / unit, wmin = std::max(1, 8 / unit);  // runs of 8 to kMarchLines lines
+    const int64_t nw = std::max<int64_t>(std::min<int64_t>(std::max<int64_t>(target, 1), (total + wmin - 1) / wmin),
+                                         (total + wmax - 1) / wmax);
+    size_t bk = 0;
+    int64_t used = 0;  // units of block mblk[bk] already dealt
+    for (int64_t w = 0; w < nw; ++w) {
+      start.push_back((int)out.size());
+      int64_t need = (w + 1) * total / nw - w * total / nw;
+      while (need > 0 && bk < mblk.size()) {
+        const int64_t units = (mblk[bk].second + unit - 1) / unit;
+        const int64_t take = std::min(need, units - used);
+        const int a = (int)(used * unit), e = (int)std::min<int64_t>((used + take) * unit, mblk[bk].second);
+        out.push_back(WorkItem{mblk[bk].first, 0, (int16_t)(e - a), a, 0});
+        used += take;
+        need -= take;
+        if (used == units) {
+          ++bk;
+          used = 0;
+        }
+      }
+    }
+    start.push_back((int)out.size());
+  };
+  if (!mblk.empty()) {
+    deal(march_f64_resident_warps(ndim_, opt.halo == 0, march_width(3)), 1, wm, wms);
+    deal(march_f64r_resident_warps(ndim_, opt.halo == 0), kResGroup, wmr, wmrs);
+  }
   auto up = [&](const void* src, size_t bytes) -> void* {
     if (bytes == 0) return nullptr;
     void* p = pool_.alloc(bytes);
@@ -447,6 +489,9 @@ void Workset::rebuild_tables() {
   d_w64_ = (WorkItem*)up(w64.data(), w64.size() * sizeof(WorkItem));
   d_wlo_ = (WorkItem*)up(wlo.data(), wlo.size() * sizeof(WorkItem));
   d_wm_ = (WorkItem*)up(wm.data(), wm.size() * sizeof(WorkItem));
+  d_wmr_ = (WorkItem*)up(wmr.data(), wmr.size() * sizeof(WorkItem));
+  d_wms_ = (int*)up(wms.data(), wms.size() * sizeof(int));
+  d_wmrs_ = (int*)up(wmrs.data(), wmrs.size() * sizeof(int));
   d_wtb_ = (WorkItem*)up(wtb.data(), wtb.size() * sizeof(WorkItem));
   d_t64_ = (CtaTask*)up(t64.data(), t64.size() * sizeof(CtaTask));
   d_tlo_ = (CtaTask*)up(tlo.data(), tlo.size() * sizeof(CtaTask));
@@ -460,6 +505,9 @@ void Workset::rebuild_tables() {
   }
   n64_ = (int)w64.size();
   nm_ = (int)wm.size();
+  nmr_ = (int)wmr.size();
+  nmw_ = wms.empty() ? 0 : (int)wms.size() - 1;
+  nmrw_ = wmrs.empty() ? 0 : (int)wmrs.size() - 1;
   ntb_ = (int)wtb.size();
   estage_ = estage;
   nlo_ = (int)wlo.size();
@@ -479,6 +527,12 @@ Tables Workset::tables() const {
   t.n64 = n64_;
   t.wm = d_wm_;
   t.nm = nm_;
+  t.wmr = d_wmr_;
+  t.nmr = nmr_;
+  t.wms = d_wms_;
+  t.nmw = nmw_;
+  t.wmrs = d_wmrs_;
+  t.nmrw = nmrw_;
   t.wtb = d_wtb_;
   t.ntb = ntb_;
   t.wlo = d_wlo_;
@@ -723,6 +777,8 @@ void Workset::sweeps_f64(int64_t n, bool resid_last) {
     prof_begin(kProfSweepF64);
     if (opt.march && ndim_ == 2 && !resid && opt.emu_adds == 0)
       LAUNCH(launch_sweep_f64_march(t, kpar, push, march_width(opt.march), cur_), "sweep f64");
+    else if (opt.march == 3 && ndim_ == 2 && opt.emu_adds == 0)
+      LAUNCH(launch_sweep_f64_march_resid(t, kpar, push, cur_), "sweep f64 + residual");
     else LAUNCH(launch_sweep_f64(t, kpar, push, resid, true, (int)opt.emu_adds, cur_), "sweep f64");
     prof_end(kProfSweepF64);
     if (!push) {
@@ -761,6 +817,8 @@ void Workset::refine_outer() {
       if (s) max_elems = std::max<int64_t>(max_elems, s->elems);
     LAUNCH(launch_refine_outer_split(t, capacity_, max_elems, epar_last_, low(), r_bf16_, cur_),
            "refine outer (split)");
+  } else if (ndim_ == 2 && opt.march == 3) {
+    LAUNCH(launch_refine_outer_march(t, epar_last_, push, low(), r_bf16_, cur_), "refine outer");
   } else {
     LAUNCH(launch_refine_outer(t, epar_last_, push, low(), r_bf16_, cur_), "refine outer");
   }

@@ -113,7 +113,7 @@ struct Options {
   int64_t autotune = 0;      // 1: pick rows/schedule by timing before the first solve
   int64_t emu_adds = 0;      // FP64 sweep: additions per warp step done on the integer pipe (0, 2, 3)
   int64_t tma = 0;           // inner sweeps (2D and 3D): stage lines in shared memory with bulk async copies
-  int64_t march = 1;         // FP64 sweeps without a residual: one warp computes all segments of a line range
+  int64_t march = 3;         // FP64 sweeps without a residual: one warp computes all segments of a line range
   int64_t outer_split = 1;   // 3D outer step as x += e over the layout, then the residual pass
   int64_t l2pf = 0;          // FP64 sweeps: lines ahead brought into L2 by bulk prefetches (0: none)
   int64_t tb = 1;            // inner sweeps two per launch (temporal blocking; 2D, fused halo, launch schedule):
@@ -236,6 +236,11 @@ class Workset {
   WorkItem* d_wlo_ = nullptr;
   WorkItem* d_wm_ = nullptr;
   int nm_ = 0;
+  WorkItem* d_wmr_ = nullptr;  // march items on residual-group boundaries (option march 3)
+  int nmr_ = 0;
+  int* d_wms_ = nullptr;   // option march 3: first item of each warp's run (wm), then the end
+  int* d_wmrs_ = nullptr;  // the same for wmr
+  int nmw_ = 0, nmrw_ = 0; // warps of the two runs tables
   WorkItem* d_wtb_ = nullptr;  // tiles of the two-sweep inner kernel
   int ntb_ = 0;
   int estage_ = 0;  // staged 3D inner sweep: e elements per stage per warp

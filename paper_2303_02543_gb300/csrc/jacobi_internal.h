@@ -149,6 +149,9 @@ struct Tables {
   const WorkItem* w64;  int n64;     // FP64 sweep / residual / refine-outer items
   const WorkItem* wlo;  int nlo;     // low-precision sweep items
   const WorkItem* wm;   int nm;      // FP64 march items (all segments of a line range)
+  const int* wms;       int nmw;     // option march 3: warp w computes items wms[w] .. wms[w+1]-1 of wm
+  const WorkItem* wmr;  int nmr;     // march items of whole residual groups (kResGroup lines)
+  const int* wmrs;      int nmrw;    // warp w computes items wmrs[w] .. wmrs[w+1]-1 of wmr
   const WorkItem* wtb;  int ntb;     // tiles of the two-sweep inner kernel (seg = tile column, n = lines)
   const FaceItem* faces; int nfaces; // interior faces
   const RedItem* red;   int nred;    // reduction CTAs
@@ -172,6 +175,15 @@ int launch_sweep_f64_march(const Tables& t, int kpar, bool push, int width, void
 // warps of the 2D march sweep resident at once on the current device (0 on
 // error or in 3D)
 int march_f64_resident_warps(int ndim, bool push, int width);
+// 2D fused-residual FP64 sweep over t.wmr (four points per lane, lines
+// staged in shared memory): bit-identical to launch_sweep_f64 with resid,
+// partials included
+int launch_sweep_f64_march_resid(const Tables& t, int kpar, bool push, void* stream);
+// 2D refinement outer step over t.wmr: bit-identical to launch_refine_outer
+int launch_refine_outer_march(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream);
+// warps of the two kernels above resident at once (the smaller count; 0 on
+// error or in 3D)
+int march_f64r_resident_warps(int ndim, bool push);
 int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, void* stream);
 // 2D inner sweep (not the first of a step) with rows staged in shared memory
 // by bulk asynchronous copies; a timed-out wait sets ctl->status bit 1.

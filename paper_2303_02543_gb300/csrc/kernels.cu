@@ -57,6 +57,14 @@ __device__ __forceinline__ double dadd1(double a, double b, double one) {
   asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(one), "d"(b));
   return r;
 }
+// a * m + b rounded once, m a multiplier held in a register (the residual's
+// t - 4 c in 2D as fma(c, -4, t): 4 c is exact, so this is the rounding of
+// the subtraction, in one FP64 instruction)
+__device__ __forceinline__ double dfma1(double a, double m, double b) {
+  double r;
+  asm("fma.rn.f64 %0, %1, %2, %3;" : "=d"(r) : "d"(a), "d"(m), "d"(b));
+  return r;
+}
 __device__ double g_fp64_one = 1.0;
 __device__ __forceinline__ double load_one() { return __ldg(&g_fp64_one); }
 
@@ -463,6 +471,11 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   const int par = (S->phase + kpar) & 1;
   const double one = load_one();
   auto add = [one](double u, double v) { return dadd1(u, v, one); };
+  double mfour = 0.0, mone = 0.0;  // -4 and -1 in registers (residual)
+  if constexpr (RESID || STORE_R) {
+    mfour = __dmul_rn(one, -4.0);
+    mone = __dmul_rn(one, -1.0);
+  }
   F64Src<MODE, TE, COH> src;
   src.unit = one;
   src.x = S->x[par];
@@ -654,9 +667,16 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
       }
     }
     if constexpr (RESID || STORE_R) {
-      // t - (2d) x as fma(t, 1, -(2d) x): the same rounding as the subtraction
-      const double r0 = add(t0, -twod_x<DIM>(c0));
-      const double r1 = add(t1, -twod_x<DIM>(c1));
+      // t - (2d) x rounded once: in 2D fma(x, -4, t) (4 x is exact); in 3D
+      // fma(6 x, -1, t) with 6 x rounded first, as the subtraction does
+      double r0, r1;
+      if constexpr (DIM == 2) {
+        r0 = dfma1(c0, mfour, t0);
+        r1 = dfma1(c1, mfour, t1);
+      } else {
+        r0 = dfma1(twod_x<DIM>(c0), mone, t0);
+        r1 = dfma1(twod_x<DIM>(c1), mone, t1);
+      }
       if constexpr (STORE_R) {
         const float rf0 = d2f(r0), rf1 = d2f(r1);
         if (v1) {
@@ -786,12 +806,112 @@ __device__ __forceinline__ void cp_async_wait_group() {
   asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
 }
 
-template <bool PUSH, int STG>
+// V values of a lane from shared memory as float (float: 16-byte aligned
+// vector reads; bfloat16: 8- or 16-byte aligned)
+template <int V>
+__device__ __forceinline__ void unpack_smem(const float* p, float (&o)[V]) {
+#pragma unroll
+  for (int q = 0; q < V / 4; ++q) {
+    const float4 a = *reinterpret_cast<const float4*>(p + 4 * q);
+    o[4 * q] = a.x; o[4 * q + 1] = a.y; o[4 * q + 2] = a.z; o[4 * q + 3] = a.w;
+  }
+}
+template <int V>
+__device__ __forceinline__ void unpack_smem(const __nv_bfloat16* p, float (&o)[V]) {
+  if constexpr (V == 4) {
+    const uint2 u = *reinterpret_cast<const uint2*>(p);
+    o[0] = __uint_as_float(u.x << 16); o[1] = __uint_as_float(u.x & 0xFFFF0000u);
+    o[2] = __uint_as_float(u.y << 16); o[3] = __uint_as_float(u.y & 0xFFFF0000u);
+  } else {
+#pragma unroll
+    for (int q = 0; q < V / 8; ++q) {
+      const uint4 u = *reinterpret_cast<const uint4*>(p + 8 * q);
+      const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        o[8 * q + 2 * j] = __uint_as_float(w4[j] << 16);
+        o[8 * q + 2 * j + 1] = __uint_as_float(w4[j] & 0xFFFF0000u);
+      }
+    }
+  }
+}
+
+// cp.async of 4 or 8 bytes (cache in L1 and L2) or 16 bytes (L2 only)
+template <int BYTES>
+__device__ __forceinline__ void cp_async_g2s(void* dst, const void* src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  if constexpr (BYTES == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
+  else asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
+}
+
+// Extra arrays of the 4-point march for the fused-residual sweep (RESID) and
+// the refinement's outer step (MODE kModeOuter).  In the outer step the field
+// the stencil reads is x_new = x + e, e (type TE) laid out like x, ghost ring
+// and columns included, and added only when `apply`; x_new is written and
+// r = t - 4 x_new is stored as TR.  RESID: r^2 is summed into the residual
+// partials, one per (group of kResGroup lines, 64-point segment), in the
+// order and through the butterfly that f64_item uses, so every partial is bit
+// for bit the one the per-segment items write.
+template <typename TE, typename TR>
+struct March4Ext {
+  const TE* __restrict__ e;
+  TR* __restrict__ r;
+  double* __restrict__ part;
+  int64_t part_off;  // B.part + B.pg * part_row
+  int part_row;
+  bool apply;
+};
+
+// doubles per staged line group of a warp: 128 x and 128 f values, and in the
+// outer step 128 e values
+template <int MODE, typename TE>
+__host__ __device__ constexpr int march4_slot_doubles() {
+  return MODE == kModeOuter ? 256 + 128 * (int)sizeof(TE) / 8 : 256;
+}
+
+// four low-precision values as float (16- or 8-byte vector load)
+template <typename TE>
+__device__ __forceinline__ void ld4_low(const TE* p, float (&v)[4]) {
+  const float4 a = ldf4<false>(p);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+
+// the valid leading values of four r values (one vector store when all four are)
+__device__ __forceinline__ void st4r_valid(float* p, const float (&v)[4], int nv) {
+  if (nv >= 4) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  } else {
+    if (nv > 0) p[0] = v[0];
+    if (nv > 1) p[1] = v[1];
+    if (nv > 2) p[2] = v[2];
+  }
+}
+__device__ __forceinline__ void st4r_valid(__nv_bfloat16* p, const float (&v)[4], int nv) {
+  if (nv >= 4) {
+    const __nv_bfloat162 a = __floats2bfloat162_rn(v[0], v[1]), b = __floats2bfloat162_rn(v[2], v[3]);
+    uint2 u;
+    memcpy(&u.x, &a, 4);
+    memcpy(&u.y, &b, 4);
+    *reinterpret_cast<uint2*>(p) = u;
+  } else {
+    if (nv > 0) p[0] = __float2bfloat16_rn(v[0]);
+    if (nv > 1) p[1] = __float2bfloat16_rn(v[1]);
+    if (nv > 2) p[2] = __float2bfloat16_rn(v[2]);
+  }
+}
+
+template <bool PUSH, int STG, int MODE = kModeSweep, bool RESID = false, typename TE = float, typename TR = float>
 __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const BlockDev& B,
                                                const BlockDev* __restrict__ blocks, const double* __restrict__ xsrc,
                                                double* __restrict__ xd, const double* __restrict__ f,
                                                const double* rd, double* wr, double one, int pf,
-                                               double* stage = nullptr) {
+                                               double* stage = nullptr, const March4Ext<TE, TR>* ex = nullptr) {
+  constexpr bool OUTER = MODE == kModeOuter;
+  constexpr int SLOT = march4_slot_doubles<MODE, TE>();
+  constexpr int NST = STG > 0 ? STG : 1;
   auto add = [one](double u, double v) { return dadd1(u, v, one); };
   const int lane = threadIdx.x & 31;
   const Geo<2> G(B, 0);
@@ -803,8 +923,19 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
   const bool holds_last = nv >= 1 && nv <= 4;    // the block's last point is x + nv - 1
   const bool east_in = lane == 31 && nv > 4;     // east of point 3 is the next segment's first point
   const int64_t gE = B.xoff + (int64_t)B.by;     // 2D: the east ghost column, one value per line
-  PushTargets T;
-  if constexpr (PUSH) push_targets<2>(T, B, blocks, 0);
+  bool apply = false;                            // outer step: x_new = x + e
+  if constexpr (OUTER) apply = ex->apply;
+  // the W / E neighbours' ghost columns, written every line by the lanes
+  // holding the block's first and last points (the S / N neighbours' ghost
+  // lines are looked up on the block's first and last line only)
+  int64_t w_col = -1, e_col = -1;
+  if constexpr (PUSH) {
+    if (x == 0 && B.nbr[0] >= 0) {
+      const BlockDev& N = blocks[B.nbr[0]];
+      w_col = N.xoff + (int64_t)N.by * N.bz;
+    }
+    if (holds_last && B.nbr[1] >= 0) e_col = blocks[B.nbr[1]].xoff;
+  }
   const int m0 = it.y0, mend = m0 + it.n;
 
   auto load4 = [&](int64_t o, double (&v)[4]) {
@@ -815,48 +946,117 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
     v[0] = v[1] = v[2] = v[3] = 0.0;
     if (valid) ldg4d(f + o, v);
   };
-  // staged form: group j holds x of line j + 1 and f of line j
+  // e at a lane's four points (outer step, once a correction exists)
+  auto load4e = [&](int64_t o, float (&v)[4]) {
+    v[0] = v[1] = v[2] = v[3] = 0.f;
+    if constexpr (OUTER) {
+      if (apply && valid) ld4_low(ex->e + o, v);
+    }
+  };
+  auto load1e = [&](int64_t o) -> float {
+    if constexpr (OUTER) {
+      if (apply) return ldf<false>(ex->e + o);
+    }
+    return 0.f;
+  };
+  // x_new = x + e at a lane's four points; called by every lane (one warp
+  // vote for the four integer-pipe conversions)
+  auto fin4 = [&](double (&v)[4], const float (&ev)[4]) {
+    if constexpr (OUTER) {
+      if (apply) {
+        double d[4];
+        bool ok[4], all = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          d[k] = f64_from_bits(f32_to_f64_bits(__float_as_uint(ev[k]), ok[k]));
+          all = all && ok[k];
+        }
+        if (!__all_sync(FULL_MASK, all)) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (!ok[k]) d[k] = slow_f2d(ev[k]);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) v[k] = add(v[k], d[k]);
+      }
+    }
+  };
+  // x + e of one value (edge lanes only: the plain conversion)
+  auto fin1 = [&](double v, float e1) {
+    if constexpr (OUTER) {
+      if (apply) return add(v, (double)e1);
+    }
+    return v;
+  };
+  // the same called by every lane (the integer-pipe conversion with a warp vote)
+  auto fin1w = [&](double v, float e1) {
+    if constexpr (OUTER) {
+      if (apply) return add(v, f2d(e1));
+    }
+    return v;
+  };
+  // staged form: group j holds x of line j + 1 and f of line j (and in the
+  // outer step e of line j + 1)
   auto issue = [&](int j) {
     if constexpr (STG > 0) {
       if (j < mend && valid) {
-        double* d = stage + ((j - m0) % (STG > 0 ? STG : 1)) * 256 + 4 * lane;
+        double* d = stage + ((j - m0) % NST) * SLOT + 4 * lane;
         const double* sx = xsrc + G.line(j + 1) + x;
         const double* sf = f + G.line(j) + x;
         cp_async16_g2s(d, sx);
         cp_async16_g2s(d + 2, sx + 2);
         cp_async16_g2s(d + 128, sf);
         cp_async16_g2s(d + 130, sf + 2);
+        if constexpr (OUTER) {
+          if (apply)
+            cp_async_g2s<4 * (int)sizeof(TE)>(reinterpret_cast<TE*>(stage + ((j - m0) % NST) * SLOT + 256) + 4 * lane,
+                                              ex->e + G.line(j + 1) + x);
+        }
       }
       cp_async_commit_group();
     }
   };
-  auto staged = [&](int j, double (&xv)[4], double (&fv)[4]) {
-    const double* d = stage + ((j - m0) % (STG > 0 ? STG : 1)) * 256 + 4 * lane;
+  auto staged = [&](int j, double (&xv)[4], double (&fv)[4], float (&ev)[4]) {
+    const double* d = stage + ((j - m0) % NST) * SLOT + 4 * lane;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       xv[k] = valid ? d[k] : 0.0;
       fv[k] = valid ? d[128 + k] : 0.0;
+      ev[k] = 0.f;
+    }
+    if constexpr (OUTER) {
+      if (apply && valid)
+        unpack_smem<4>(reinterpret_cast<const TE*>(stage + ((j - m0) % NST) * SLOT + 256) + 4 * lane, ev);
     }
   };
   // prologue: lines m0 - 1 (p), m0 (c), m0 + 1 (n); pairs Q(m0 - 1, x_k)
   double p[4], c[4], n[4], fc[4], Qp[4];
-  load4(G.line(m0 - 1) + x, p);
-  load4(G.line(m0) + x, c);
-  if constexpr (STG > 0) {
+  {
+    float ep[4], ec[4], en0[4];
+    load4(G.line(m0 - 1) + x, p);
+    load4(G.line(m0) + x, c);
+    load4e(G.line(m0 - 1) + x, ep);
+    load4e(G.line(m0) + x, ec);
+    if constexpr (STG > 0) {
 #pragma unroll
-    for (int j = 0; j < STG; ++j) issue(m0 + j);
-    cp_async_wait_group<STG - 1>();
-    staged(m0, n, fc);
-  } else {
-    load4(G.line(m0 + 1) + x, n);
-    loadf(G.line(m0) + x, fc);
+      for (int j = 0; j < STG; ++j) issue(m0 + j);
+      cp_async_wait_group<NST - 1>();
+      staged(m0, n, fc, en0);
+    } else {
+      load4(G.line(m0 + 1) + x, n);
+      loadf(G.line(m0) + x, fc);
+      load4e(G.line(m0 + 1) + x, en0);
+    }
+    fin4(p, ep);
+    fin4(c, ec);
+    fin4(n, en0);
   }
   double ce = 0.0, ge = 0.0, pe = 0.0;
   if (east_in) {
-    ce = __ldg(xsrc + G.line(m0) + x + 4);
-    pe = __ldg(xsrc + G.line(m0 - 1) + x + 4);
+    ce = fin1(__ldg(xsrc + G.line(m0) + x + 4), load1e(G.line(m0) + x + 4));
+    pe = fin1(__ldg(xsrc + G.line(m0 - 1) + x + 4), load1e(G.line(m0 - 1) + x + 4));
   }
-  if (holds_last) ge = __ldg(xsrc + gE + m0);
+  if (holds_last) ge = fin1(__ldg(xsrc + gE + m0), load1e(gE + m0));
   {
     double pn = __shfl_down_sync(FULL_MASK, p[0], 1);
     if (east_in) pn = pe;
@@ -865,7 +1065,10 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
     Qp[2] = add(p[3], c[2]);
     Qp[3] = add(pn, c[3]);
   }
-#pragma unroll 2
+  double mfour = 0.0;  // -4 in a register (residual)
+  if constexpr (RESID || OUTER) mfour = __dmul_rn(one, -4.0);
+  double qa0 = 0.0, qa1 = 0.0;  // RESID: this lane's r^2 of points 0-1 and of points 2-3 over the current group
+#pragma unroll 1
   for (int m = m0; m < mend; ++m) {
     const bool more = m + 1 < mend;
     // lines pf steps ahead of the register loads into L2 (within this item's
@@ -877,7 +1080,9 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
     }
     // loads for the next line: x of line m + 2, f and the edge values of line m + 1
     double nn[4], fn[4];
+    float en[4];
     double cen = 0.0, gen = 0.0;
+    float cee = 0.f, gee = 0.f;
     if constexpr (STG > 0) {
       issue(m + STG);  // group m + STG into the slot group m has left
     }
@@ -885,12 +1090,22 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
       if constexpr (STG == 0) {
         load4(G.line(m + 2) + x, nn);
         loadf(G.line(m + 1) + x, fn);
+        load4e(G.line(m + 2) + x, en);
       }
-      if (east_in) cen = __ldg(xsrc + G.line(m + 1) + x + 4);
-      if (holds_last) gen = __ldg(xsrc + gE + m + 1);
+      if (east_in) {
+        cen = __ldg(xsrc + G.line(m + 1) + x + 4);
+        cee = load1e(G.line(m + 1) + x + 4);
+      }
+      if (holds_last) {
+        gen = __ldg(xsrc + gE + m + 1);
+        gee = load1e(gE + m + 1);
+      }
     } else {
 #pragma unroll
-      for (int k = 0; k < 4; ++k) nn[k] = fn[k] = 0.0;
+      for (int k = 0; k < 4; ++k) {
+        nn[k] = fn[k] = 0.0;
+        en[k] = 0.f;
+      }
     }
     // Q(m, x_k) = x[m][x_k + 1] + x[m + 1][x_k]; the block's last point takes the ghost
     double ceast = __shfl_down_sync(FULL_MASK, c[0], 1);
@@ -911,40 +1126,102 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
     t[1] = add(add(Qp[0], Q[1]), fc[1]);
     t[2] = add(add(Qp[1], Q[2]), fc[2]);
     t[3] = add(add(Qp[2], Q[3]), fc[3]);
-    // t / 4 on the integer pipe; one warp vote for the four points
     double o[4];
-    bool fast = true;
+    if constexpr (MODE == kModeSweep) {
+      // t / 4 on the integer pipe; one warp vote for the four points
+      bool fast = true;
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint64_t b = f64_bits(t[k]);
-      o[k] = quarter_bits(b);
-      fast = fast && (quarter_fast(b) || k >= nv);
-    }
-    if (!__all_sync(FULL_MASK, fast)) {
+      for (int k = 0; k < 4; ++k) {
+        const uint64_t b = f64_bits(t[k]);
+        o[k] = quarter_bits(b);
+        fast = fast && (quarter_fast(b) || k >= nv);
+      }
+      if (!__all_sync(FULL_MASK, fast)) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
-        if (k < nv && !quarter_fast(f64_bits(t[k]))) o[k] = slow_quarter(t[k]);
+        for (int k = 0; k < 4; ++k)
+          if (k < nv && !quarter_fast(f64_bits(t[k]))) o[k] = slow_quarter(t[k]);
+      }
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) o[k] = c[k];  // outer step: the updated iterate itself
     }
     if (valid) {
       st4d_valid(xd + G.line(m) + x, o, nv);
       if constexpr (PUSH) {
-        if (m == 0 && T.lo_line >= 0) st4d_valid(xd + T.lo_line + x, o, nv);
-        if (m == G.extent - 1 && T.hi_line >= 0) st4d_valid(xd + T.hi_line + x, o, nv);
-        if (x == 0 && T.w_col >= 0) xd[T.w_col + m] = o[0];
-        if (holds_last && T.e_col >= 0) {
+        if (m == 0) {  // the S neighbour's north ghost line
+          const int nb = __ldg(&blocks[it.block].nbr[2]);
+          if (nb >= 0) {
+            const BlockDev& N = blocks[nb];
+            st4d_valid(xd + N.off + (int64_t)(N.by + 1) * N.pitch + x, o, nv);
+          }
+        }
+        if (m == G.extent - 1) {  // the N neighbour's south ghost line
+          const int nb = __ldg(&blocks[it.block].nbr[3]);
+          if (nb >= 0) st4d_valid(xd + blocks[nb].off + x, o, nv);
+        }
+        if (w_col >= 0) xd[w_col + m] = o[0];
+        if (e_col >= 0) {
           double last = o[0];
 #pragma unroll
           for (int k = 1; k < 4; ++k)
             if (k == nv - 1) last = o[k];
-          xd[T.e_col + m] = last;
+          xd[e_col + m] = last;
+        }
+      }
+    }
+    if constexpr (RESID || OUTER) {
+      // r = t - 4 c rounded once, as fma(c, -4, t) (4 c is exact)
+      double r[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) r[k] = dfma1(c[k], mfour, t[k]);
+      if constexpr (OUTER) {
+        float rf[4];
+        bool okf[4], allf = true;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+          rf[k] = __uint_as_float(f64_to_f32_bits(f64_bits(r[k]), okf[k]));
+          allf = allf && (okf[k] || k >= nv);
+        }
+        if (!__all_sync(FULL_MASK, allf)) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k)
+            if (k < nv && !okf[k]) rf[k] = slow_d2f(r[k]);
+        }
+        if (valid) st4r_valid(ex->r + G.line(m) + x, rf, nv);
+      }
+      if constexpr (RESID) {
+        // points 0-1 and 2-3 of this lane are the two points of lanes
+        // 2l and 2l + 1 of f64_item's 64-point segment (lanes 0-15 form
+        // segment 2 sg, lanes 16-31 segment 2 sg + 1)
+        if (nv > 0) qa0 = __fma_rn(r[0], r[0], qa0);
+        if (nv > 1) qa0 = __fma_rn(r[1], r[1], qa0);
+        if (nv > 2) qa1 = __fma_rn(r[2], r[2], qa1);
+        if (nv > 3) qa1 = __fma_rn(r[3], r[3], qa1);
+        if ((m + 1) % kResGroup == 0 || m + 1 == G.extent) {
+          // f64_item's butterfly over 32 lanes (xor 16, 8, 4, 2, 1) is, on
+          // these lanes, xor 8, 4, 2, 1 then the lane's own two sums
+#pragma unroll
+          for (int s = 8; s > 0; s >>= 1) {
+            qa0 = add(qa0, __shfl_xor_sync(FULL_MASK, qa0, s));
+            qa1 = add(qa1, __shfl_xor_sync(FULL_MASK, qa1, s));
+          }
+          const double q = add(qa0, qa1);
+          const int half = lane >> 4;
+          if ((lane & 15) == 0 && xs + 64 * half < bx)
+            ex->part[ex->part_off + (int64_t)(m / kResGroup) * ex->part_row + 2 * sg + half] = q;
+          qa0 = 0.0;
+          qa1 = 0.0;
         }
       }
     }
     if constexpr (STG > 0) {
       if (more) {
-        cp_async_wait_group<STG - 1>();  // group m + 1 has landed
-        staged(m + 1, nn, fn);
+        cp_async_wait_group<NST - 1>();  // group m + 1 has landed
+        staged(m + 1, nn, fn, en);
       }
+    }
+    if constexpr (OUTER) {
+      if (more) fin4(nn, en);
     }
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
@@ -953,44 +1230,88 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
       n[k] = nn[k];
       fc[k] = fn[k];
     }
-    ce = cen;
-    ge = gen;
+    if constexpr (OUTER) {
+      // lane 31's east value and the last point's ghost: one instruction
+      const double v = fin1w(east_in ? cen : gen, east_in ? cee : gee);
+      ce = v;
+      ge = v;
+    } else {
+      ce = cen;
+      ge = gen;
+    }
   }
   if constexpr (STG > 0) cp_async_wait_group<0>();  // nothing may still target this warp's ring
 }
 
 constexpr int kMarchStages = 4;  // lines staged ahead by the shared-memory form of the 4-point march
 
-template <bool PUSH, int STG>
+// MODE kModeSweep without RESID: the plain sweep; with RESID: the sweep that
+// also writes the residual partials of its input.  MODE kModeOuter (RESID):
+// the refinement's outer step, e from buffer epar.
+//
+// wstart == nullptr: warp w computes item w (nwarps = the item count).
+// Otherwise warp w computes items wstart[w] .. wstart[w + 1] - 1 in turn: the
+// lines of all blocks are dealt out in equal runs, one per resident warp, and
+// a run that crosses a block boundary is two items, so every warp (and every
+// SM) gets the same share of the sweep.
+template <bool PUSH, int STG, int MODE = kModeSweep, bool RESID = false, typename TE = float, typename TR = float>
 __global__ void __launch_bounds__(kThreads, 2)
-k_f64_march4(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
-             const SolveDev* __restrict__ solves, int pf) {
+k_f64_march4(const WorkItem* __restrict__ items, int nwarps, const int* __restrict__ wstart, int kpar,
+             const BlockDev* __restrict__ blocks, const SolveDev* __restrict__ solves, int pf, int epar) {
+  constexpr bool OUTER = MODE == kModeOuter;
+  constexpr int SLOT = march4_slot_doubles<MODE, TE>();
   __shared__ double pairs[kWarps][2][kMarchLines];
-  extern __shared__ __align__(16) double march_stage[];  // STG * 256 doubles per warp when STG > 0
+  extern __shared__ __align__(16) double march_stage[];  // STG * SLOT doubles per warp when STG > 0
   const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int w = blockIdx.x * kWarps + wi;
-  if (w >= nitems) return;
-  const WorkItem it = items[w];
-  const BlockDev B = blocks[it.block];
-  const SolveDev* S = solves + B.solve;
-  if (!S->active) return;
-  const int par = (S->phase + kpar) & 1;
-  const double* __restrict__ xsrc = S->x[par];
-  double* __restrict__ xd = S->x[par ^ 1];
-  const double one = load_one();
-  // (W + S) pairs of the block's first column, x[m][-1] + x[m - 1][0], one
-  // line per lane, into the buffer lane 0 of segment 0 reads
-  const Geo<2> G(B, 0);
-  for (int j = lane; j < it.n; j += 32) {
-    const int m = it.y0 + j;
-    pairs[wi][1][j] = dadd1(__ldg(xsrc + B.xoff + m), __ldg(xsrc + G.line(m - 1)), one);
+  if (w >= nwarps) return;
+  int k0 = w, k1 = w + 1;
+  if (wstart) {
+    k0 = wstart[w];
+    k1 = wstart[w + 1];
   }
-  __syncwarp();
-  const int nseg = (B.bx + kSegF64x4 - 1) / kSegF64x4;
-  for (int sg = 0; sg < nseg; ++sg) {
-    f64_march4_seg<PUSH, STG>(it, sg, B, blocks, xsrc, xd, S->f, pairs[wi][(sg + 1) & 1], pairs[wi][sg & 1], one,
-                              pf, STG > 0 ? march_stage + wi * STG * 256 : nullptr);
+  const double one = load_one();
+  for (int k = k0; k < k1; ++k) {
+    const WorkItem it = items[k];
+    const BlockDev B = blocks[it.block];
+    const SolveDev* S = solves + B.solve;
+    if (!S->active) continue;
+    const int par = (S->phase + kpar) & 1;
+    const double* __restrict__ xsrc = S->x[par];
+    double* __restrict__ xd = S->x[par ^ 1];
+    March4Ext<TE, TR> ex{};
+    if constexpr (OUTER || RESID) {
+      if constexpr (OUTER) {
+        ex.e = reinterpret_cast<const TE*>(S->e[epar]);
+        ex.r = reinterpret_cast<TR*>(S->r);
+        ex.apply = S->apply_e != 0;
+      }
+      ex.part = S->part;
+      ex.part_off = B.part + (int64_t)B.pg * S->part_row;
+      ex.part_row = S->part_row;
+    }
+    // (W + S) pairs of the block's first column, x[m][-1] + x[m - 1][0], one
+    // line per lane, into the buffer lane 0 of segment 0 reads
+    const Geo<2> G(B, 0);
+    for (int j = lane; j < it.n; j += 32) {
+      const int m = it.y0 + j;
+      double wv = __ldg(xsrc + B.xoff + m), sv = __ldg(xsrc + G.line(m - 1));
+      if constexpr (OUTER) {
+        if (ex.apply) {
+          wv = dadd1(wv, (double)ldf<false>(ex.e + B.xoff + m), one);
+          sv = dadd1(sv, (double)ldf<false>(ex.e + G.line(m - 1)), one);
+        }
+      }
+      pairs[wi][1][j] = dadd1(wv, sv, one);
+    }
     __syncwarp();
+    const int nseg = (B.bx + kSegF64x4 - 1) / kSegF64x4;
+    for (int sg = 0; sg < nseg; ++sg) {
+      f64_march4_seg<PUSH, STG, MODE, RESID, TE, TR>(it, sg, B, blocks, xsrc, xd, S->f, pairs[wi][(sg + 1) & 1],
+                                                     pairs[wi][sg & 1], one, pf,
+                                                     STG > 0 ? march_stage + wi * STG * SLOT : nullptr, &ex);
+      __syncwarp();
+    }
   }
 }
 
@@ -1399,43 +1720,6 @@ __device__ __forceinline__ void tb_ld4(const T* p, float (&v)[4]) {
   ldv<false, 4>(p, v);
 }
 
-// V values of a lane from shared memory as float (float: 16-byte aligned
-// vector reads; bfloat16: 8- or 16-byte aligned)
-template <int V>
-__device__ __forceinline__ void unpack_smem(const float* p, float (&o)[V]) {
-#pragma unroll
-  for (int q = 0; q < V / 4; ++q) {
-    const float4 a = *reinterpret_cast<const float4*>(p + 4 * q);
-    o[4 * q] = a.x; o[4 * q + 1] = a.y; o[4 * q + 2] = a.z; o[4 * q + 3] = a.w;
-  }
-}
-template <int V>
-__device__ __forceinline__ void unpack_smem(const __nv_bfloat16* p, float (&o)[V]) {
-  if constexpr (V == 4) {
-    const uint2 u = *reinterpret_cast<const uint2*>(p);
-    o[0] = __uint_as_float(u.x << 16); o[1] = __uint_as_float(u.x & 0xFFFF0000u);
-    o[2] = __uint_as_float(u.y << 16); o[3] = __uint_as_float(u.y & 0xFFFF0000u);
-  } else {
-#pragma unroll
-    for (int q = 0; q < V / 8; ++q) {
-      const uint4 u = *reinterpret_cast<const uint4*>(p + 8 * q);
-      const uint32_t w4[4] = {u.x, u.y, u.z, u.w};
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        o[8 * q + 2 * j] = __uint_as_float(w4[j] << 16);
-        o[8 * q + 2 * j + 1] = __uint_as_float(w4[j] & 0xFFFF0000u);
-      }
-    }
-  }
-}
-
-// cp.async of 4 or 8 bytes (cache in L1 and L2) or 16 bytes (L2 only)
-template <int BYTES>
-__device__ __forceinline__ void cp_async_g2s(void* dst, const void* src) {
-  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-  if constexpr (BYTES == 16) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
-  else asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d), "l"(src), "n"(BYTES) : "memory");
-}
 
 // PERSIST = false (default): one CTA per tile, one buffer; the loads of a
 // tile are all in flight at once and the resident CTAs of an SM overlap one
@@ -2736,7 +3020,10 @@ static int sweep_f64_dim(const Tables& t, int kpar, bool push, bool resid, bool 
   return (int)cudaGetLastError();
 }
 
-static constexpr int march_stage_bytes() { return kWarps * kMarchStages * 256 * (int)sizeof(double); }
+template <int MODE = kModeSweep, typename TE = float>
+static constexpr int march_stage_bytes() {
+  return kWarps * kMarchStages * march4_slot_doubles<MODE, TE>() * (int)sizeof(double);
+}
 
 // width: 2 (64-point segments), 4 (128-point segments, register prefetch),
 // 5 (128-point segments, lines staged in shared memory)
@@ -2750,10 +3037,11 @@ int launch_sweep_f64_march(const Tables& t, int kpar, bool push, int width, void
     auto k = push ? k_f64_march4<true, kMarchStages> : k_f64_march4<false, kMarchStages>;
     const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
     if (e != cudaSuccess) return (int)e;
-    k<<<g, b, sm, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
+    if (t.nmw == 0) return 0;
+    k<<<grid_of(t.nmw, kWarps), b, sm, s>>>(t.wm, t.nmw, t.wms, kpar, t.blocks, t.solves, t.l2pf, 0);
   } else if (width == 4) {
-    if (push) k_f64_march4<true, 0><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
-    else k_f64_march4<false, 0><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
+    if (push) k_f64_march4<true, 0><<<g, b, 0, s>>>(t.wm, t.nm, nullptr, kpar, t.blocks, t.solves, t.l2pf, 0);
+    else k_f64_march4<false, 0><<<g, b, 0, s>>>(t.wm, t.nm, nullptr, kpar, t.blocks, t.solves, t.l2pf, 0);
   } else {
     if (push) k_f64_march<2, true><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
     else k_f64_march<2, false><<<g, b, 0, s>>>(t.wm, t.nm, kpar, t.blocks, t.solves, t.l2pf);
@@ -2779,6 +3067,64 @@ int march_f64_resident_warps(int ndim, bool push, int width) {
     e = push ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march<2, true>, kThreads, 0)
              : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_f64_march<2, false>, kThreads, 0);
   if (e != cudaSuccess) return 0;
+  return per_sm * sms * kWarps;
+}
+
+// The fused-residual sweep and the outer step over the residual-aligned march
+// items (t.wmr), four points per lane, lines staged in shared memory.
+template <bool PUSH, int MODE, typename TE, typename TR>
+static cudaError_t march4r_launch(const Tables& t, int kpar, int epar, cudaStream_t s) {
+  if (t.nmrw == 0) return cudaSuccess;
+  constexpr int sm = march_stage_bytes<MODE, TE>();
+  auto k = k_f64_march4<PUSH, kMarchStages, MODE, true, TE, TR>;
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return e;
+  k<<<grid_of(t.nmrw, kWarps), kThreads, sm, s>>>(t.wmr, t.nmrw, t.wmrs, kpar, t.blocks, t.solves, t.l2pf, epar);
+  return cudaGetLastError();
+}
+
+template <bool PUSH, int MODE, typename TE, typename TR>
+static int march4r_per_sm() {
+  constexpr int sm = march_stage_bytes<MODE, TE>();
+  auto k = k_f64_march4<PUSH, kMarchStages, MODE, true, TE, TR>;
+  int per_sm = 0;
+  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kThreads, sm);
+  return e == cudaSuccess ? per_sm : 0;
+}
+
+int launch_sweep_f64_march_resid(const Tables& t, int kpar, bool push, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.ndim != 2) return (int)cudaErrorInvalidValue;
+  return (int)(push ? march4r_launch<true, kModeSweep, float, float>(t, kpar, 0, s)
+                    : march4r_launch<false, kModeSweep, float, float>(t, kpar, 0, s));
+}
+
+int launch_refine_outer_march(const Tables& t, int epar_last, bool push, int low, bool r_bf16, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.ndim != 2) return (int)cudaErrorInvalidValue;
+  cudaError_t e;
+  if (low == kLowF32)
+    e = push ? march4r_launch<true, kModeOuter, float, float>(t, 0, epar_last, s)
+             : march4r_launch<false, kModeOuter, float, float>(t, 0, epar_last, s);
+  else if (r_bf16)
+    e = push ? march4r_launch<true, kModeOuter, __nv_bfloat16, __nv_bfloat16>(t, 0, epar_last, s)
+             : march4r_launch<false, kModeOuter, __nv_bfloat16, __nv_bfloat16>(t, 0, epar_last, s);
+  else
+    e = push ? march4r_launch<true, kModeOuter, __nv_bfloat16, float>(t, 0, epar_last, s)
+             : march4r_launch<false, kModeOuter, __nv_bfloat16, float>(t, 0, epar_last, s);
+  return (int)e;
+}
+
+int march_f64r_resident_warps(int ndim, bool push) {
+  int dev = 0, sms = 0;
+  if (ndim != 2) return 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  // the fewest resident CTAs of the kernels that run over these items
+  int per_sm = push ? march4r_per_sm<true, kModeSweep, float, float>() : march4r_per_sm<false, kModeSweep, float, float>();
+  per_sm = std::min(per_sm, push ? march4r_per_sm<true, kModeOuter, float, float>()
+                                 : march4r_per_sm<false, kModeOuter, float, float>());
   return per_sm * sms * kWarps;
 }
 

@@ -355,8 +355,8 @@ def test_integer_pipe_additions_bit_exact(emu, dims, block):
                                         ((512, 100), (128, 50)), ((7, 9), (2, 4))])
 def test_march_items_bit_exact(halo, dims, block):
     """One warp over all segments of a line range (edge pairs handed on in
-    shared memory), with two (march = 1) or four (march = 2) points per lane,
-    gives the bits of the per-segment items and of the oracle."""
+    shared memory), with two (march = 1) or four (march = 2, 3) points per
+    lane, gives the bits of the per-segment items and of the oracle."""
     p = inputs.make_problem(dims, block, 59, boundary="uniform", source="normal", x0="uniform")
     out = {}
     for march in (0, 1, 2, 3):
@@ -372,6 +372,61 @@ def test_march_items_bit_exact(halo, dims, block):
     assert np.array_equal(out[3], out[0])
     assert np.array_equal(out["pf"], out[0])
     assert np.array_equal(out[1], oracle.sweeps(p.dims, p.faces, p.source, p.x0, 9))
+
+
+MARCH_R_CASES = [((60, 45), (32, 16)), ((130, 77), (64, 32)), ((5, 33), (5, 11)), ((129, 40), (129, 40)),
+                 ((383, 70), (127, 70)), ((512, 100), (128, 50)), ((7, 9), (2, 4)), ((300, 190), (300, 190)),
+                 ((65, 1), (64, 1)), ((200, 3), (50, 3)), ((1000, 300), (200, 150))]
+
+
+@pytest.mark.parametrize("halo", [0, 1])
+@pytest.mark.parametrize("dims,block", MARCH_R_CASES)
+def test_march_fused_residual_sweep_bit_exact(halo, dims, block):
+    """The fused-residual FP64 sweep over march items whose line ranges are
+    whole residual groups (four points per lane, lines staged; march = 3)
+    writes the field and the residual partials of the per-segment items bit
+    for bit: the same status, sweep count, relative residual at every check
+    and field as march = 0, and the oracle's solve rule."""
+    p = inputs.make_problem(dims, block, 61, boundary="uniform", source="normal", x0="uniform")
+    out = {}
+    for march in (0, 3):
+        with solver(p, march=march, halo=halo, check_every=9) as s:
+            st, sw, rel = s.solve(1e-14, 95)
+            x1 = s.field()
+            st2, sw2, rel2 = s.solve(1e-15, 20)
+            out[march] = (st, sw, rel, st2, sw2, rel2, x1, s.field())
+    assert out[3][:6] == out[0][:6]
+    assert np.array_equal(out[3][6], out[0][6]) and np.array_equal(out[3][7], out[0][7])
+    st_o, x_o, sw_o, rel_o = oracle.solve(p.dims, p.faces, p.source, p.x0, 1e-14, 95, 9)
+    assert out[3][0] == st_o and out[3][1] == sw_o
+    assert abs(out[3][2] - rel_o) <= 1e-10 * rel_o
+    assert np.array_equal(out[3][6], x_o)
+
+
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False),
+                                           ("bf16r16_refine", True, True)])
+@pytest.mark.parametrize("halo", [0, 1])
+@pytest.mark.parametrize("dims,block,period", [((60, 45), (32, 16), 20), ((130, 77), (64, 32), 7),
+                                               ((5, 33), (5, 11), 10), ((383, 70), (127, 70), 9),
+                                               ((7, 9), (2, 4), 5), ((257, 40), (128, 20), 11)])
+def test_march_outer_step_bit_exact(dtype, e16, r16, halo, dims, block, period):
+    """The refinement's outer step (x_new = x + e, r = b - A x_new stored in
+    the low type, residual partials) over residual-aligned march items: the
+    same status, inner-sweep count, relative residual and field as the
+    per-segment items, and the oracle's emulation."""
+    p = inputs.make_problem(dims, block, 62, boundary="uniform", source="normal", x0="zero")
+    res = {}
+    for march in (0, 3):
+        with solver(p, dtype=dtype, refine_period=period, march=march, halo=halo) as s:
+            st, sw, rel = s.solve(1e-8, 10 ** 6)
+            res[march] = (st, sw, rel, s.field())
+    assert res[3][:3] == res[0][:3]
+    assert np.array_equal(res[3][3], res[0][3])
+    st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, period,
+                                             e_bf16=e16, r_bf16=r16)
+    assert res[3][0] == J.OK and st_o == oracle.OK
+    assert res[3][1] == sw_o
+    assert np.array_equal(res[3][3], x_o)
 
 
 def test_residual_decomposition_independent_3d():
