@@ -1000,7 +1000,7 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
   auto issue = [&](int j) {
     if constexpr (STG > 0) {
       if (j < mend && valid) {
-        double* d = stage + ((j - m0) % NST) * SLOT + 4 * lane;
+        double* d = stage + ((unsigned)(j - m0) % (unsigned)NST) * SLOT + 4 * lane;
         const double* sx = xsrc + G.line(j + 1) + x;
         const double* sf = f + G.line(j) + x;
         cp_async16_g2s(d, sx);
@@ -1009,27 +1009,34 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
         cp_async16_g2s(d + 130, sf + 2);
         if constexpr (OUTER) {
           if (apply)
-            cp_async_g2s<4 * (int)sizeof(TE)>(reinterpret_cast<TE*>(stage + ((j - m0) % NST) * SLOT + 256) + 4 * lane,
+            cp_async_g2s<4 * (int)sizeof(TE)>(reinterpret_cast<TE*>(stage + ((unsigned)(j - m0) % (unsigned)NST) * SLOT + 256) + 4 * lane,
                                               ex->e + G.line(j + 1) + x);
         }
       }
       cp_async_commit_group();
     }
   };
-  auto staged = [&](int j, double (&xv)[4], double (&fv)[4], float (&ev)[4]) {
-    const double* d = stage + ((j - m0) % NST) * SLOT + 4 * lane;
+  // x (and e) of line j + 1 from group j; f of line j is read where the line
+  // is computed (staged_f), just before group j's slot is reissued
+  auto staged = [&](int j, double (&xv)[4], float (&ev)[4]) {
+    const double* d = stage + ((unsigned)(j - m0) % (unsigned)NST) * SLOT + 4 * lane;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       xv[k] = valid ? d[k] : 0.0;
-      fv[k] = valid ? d[128 + k] : 0.0;
       ev[k] = 0.f;
     }
     if constexpr (OUTER) {
       if (apply && valid)
-        unpack_smem<4>(reinterpret_cast<const TE*>(stage + ((j - m0) % NST) * SLOT + 256) + 4 * lane, ev);
+        unpack_smem<4>(reinterpret_cast<const TE*>(stage + ((unsigned)(j - m0) % (unsigned)NST) * SLOT + 256) + 4 * lane, ev);
     }
   };
-  // prologue: lines m0 - 1 (p), m0 (c), m0 + 1 (n); pairs Q(m0 - 1, x_k)
+  auto staged_f = [&](int j, double (&fv)[4]) {
+    const double* d = stage + ((unsigned)(j - m0) % (unsigned)NST) * SLOT + 128 + 4 * lane;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) fv[k] = valid ? d[k] : 0.0;
+  };
+  // prologue: lines m0 - 1 (p), m0 (c), m0 + 1 (n); pairs Q(m0 - 1, x_k);
+  // fc: f of line m0 (register form only)
   double p[4], c[4], n[4], fc[4], Qp[4];
   {
     float ep[4], ec[4], en0[4];
@@ -1041,7 +1048,7 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
 #pragma unroll
       for (int j = 0; j < STG; ++j) issue(m0 + j);
       cp_async_wait_group<NST - 1>();
-      staged(m0, n, fc, en0);
+      staged(m0, n, en0);
     } else {
       load4(G.line(m0 + 1) + x, n);
       loadf(G.line(m0) + x, fc);
@@ -1083,9 +1090,6 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
     float en[4];
     double cen = 0.0, gen = 0.0;
     float cee = 0.f, gee = 0.f;
-    if constexpr (STG > 0) {
-      issue(m + STG);  // group m + STG into the slot group m has left
-    }
     if (more) {
       if constexpr (STG == 0) {
         load4(G.line(m + 2) + x, nn);
@@ -1121,11 +1125,19 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
     double w0 = __shfl_up_sync(FULL_MASK, Qp[3], 1);
     if (lane == 31) wr[m - m0] = Qp[3];
     if (lane == 0) w0 = rd[m - m0];
+    double fm[4];  // f of line m
+    if constexpr (STG > 0) {
+      staged_f(m, fm);
+      issue(m + STG);  // group m + STG into the slot group m leaves now
+    } else {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) fm[k] = fc[k];
+    }
     double t[4];
-    t[0] = add(add(w0, Q[0]), fc[0]);
-    t[1] = add(add(Qp[0], Q[1]), fc[1]);
-    t[2] = add(add(Qp[1], Q[2]), fc[2]);
-    t[3] = add(add(Qp[2], Q[3]), fc[3]);
+    t[0] = add(add(w0, Q[0]), fm[0]);
+    t[1] = add(add(Qp[0], Q[1]), fm[1]);
+    t[2] = add(add(Qp[1], Q[2]), fm[2]);
+    t[3] = add(add(Qp[2], Q[3]), fm[3]);
     double o[4];
     if constexpr (MODE == kModeSweep) {
       // t / 4 on the integer pipe; one warp vote for the four points
@@ -1217,7 +1229,7 @@ __device__ __forceinline__ void f64_march4_seg(const WorkItem& it, int sg, const
     if constexpr (STG > 0) {
       if (more) {
         cp_async_wait_group<NST - 1>();  // group m + 1 has landed
-        staged(m + 1, nn, fn, en);
+        staged(m + 1, nn, en);
       }
     }
     if constexpr (OUTER) {
