@@ -495,8 +495,17 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   const bool east_inner = x + 2 < bx;
   const int64_t gW = B.xoff;
   const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
-  PushTargets T;
-  if constexpr (PUSH && WRITE) push_targets<DIM>(T, B, blocks, y);
+  // halo push: the W / E neighbours' ghost columns are kept by the lanes
+  // holding the block's first and last points; the march-axis faces and (3D)
+  // the side rows are looked up on the lines that write them
+  int64_t w_col = -1, e_col = -1;
+  if constexpr (PUSH && WRITE) {
+    if (x == 0 && B.nbr[0] >= 0) {
+      const BlockDev& N = blocks[B.nbr[0]];
+      w_col = N.xoff + (int64_t)N.by * N.bz;  // the west neighbour's east ghost column
+    }
+    if ((last0 || last1) && B.nbr[1] >= 0) e_col = blocks[B.nbr[1]].xoff;  // the east neighbour's west column
+  }
 
   const int m0 = DIM == 2 ? it.y0 : it.z0;
   const int mend = m0 + it.n;
@@ -639,30 +648,45 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
       if (v1) *reinterpret_cast<double2*>(d) = make_double2(o0, o1);
       else if (v0) *d = o0;
       if constexpr (PUSH) {
-        if (m == 0 && T.lo_line >= 0) {
-          if (v1) *reinterpret_cast<double2*>(xd + T.lo_line + x) = make_double2(o0, o1);
-          else if (v0) xd[T.lo_line + x] = o0;
+        auto put2 = [&](double* q) {
+          if (v1) *reinterpret_cast<double2*>(q) = make_double2(o0, o1);
+          else if (v0) *q = o0;
+        };
+        constexpr int lo = DIM == 2 ? 2 : 4;  // the march-axis faces
+        if (m == 0) {
+          const int nb = __ldg(&blocks[it.block].nbr[lo]);
+          if (nb >= 0) {
+            const Geo<DIM> GN(blocks[nb], y);
+            put2(xd + GN.line(GN.extent) + x);
+          }
         }
-        if (m == G.extent - 1 && T.hi_line >= 0) {
-          if (v1) *reinterpret_cast<double2*>(xd + T.hi_line + x) = make_double2(o0, o1);
-          else if (v0) xd[T.hi_line + x] = o0;
+        if (m == G.extent - 1) {
+          const int nb = __ldg(&blocks[it.block].nbr[lo + 1]);
+          if (nb >= 0) {
+            const Geo<DIM> GN(blocks[nb], y);
+            put2(xd + GN.line(-1) + x);
+          }
         }
         if constexpr (DIM == 3) {
-          if (T.lo_side >= 0) {
-            double* q = xd + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x;
-            if (v1) *reinterpret_cast<double2*>(q) = make_double2(o0, o1);
-            else if (v0) *q = o0;
+          if (y == 0) {  // the S neighbour's north ghost row of plane m
+            const int nb = __ldg(&blocks[it.block].nbr[2]);
+            if (nb >= 0) {
+              const BlockDev& N = blocks[nb];
+              put2(xd + N.off + (int64_t)(N.by + 1) * N.pitch + (int64_t)(m + 1) * N.plane + x);
+            }
           }
-          if (T.hi_side >= 0) {
-            double* q = xd + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x;
-            if (v1) *reinterpret_cast<double2*>(q) = make_double2(o0, o1);
-            else if (v0) *q = o0;
+          if (y == B.by - 1) {  // the N neighbour's south ghost row of plane m
+            const int nb = __ldg(&blocks[it.block].nbr[3]);
+            if (nb >= 0) {
+              const BlockDev& N = blocks[nb];
+              put2(xd + N.off + (int64_t)(m + 1) * N.plane + x);
+            }
           }
         }
-        if (x == 0 && T.w_col >= 0) xd[T.w_col + col] = o0;
-        if (T.e_col >= 0) {
-          if (last0) xd[T.e_col + col] = o0;
-          if (last1) xd[T.e_col + col] = o1;
+        if (w_col >= 0) xd[w_col + col] = o0;
+        if (e_col >= 0) {
+          if (last0) xd[e_col + col] = o0;
+          if (last1) xd[e_col + col] = o1;
         }
       }
     }
