@@ -1195,6 +1195,7 @@ void Workset::autotune() {
   if (!ref && ndim_ == 2) {
     cands.push_back(Cand{32, 0, 1, 0});
     cands.push_back(Cand{32, 0, 2, 0});
+    cands.push_back(Cand{32, 0, 3, 0});
   }
   // 2D inner sweeps two per launch (even sweep counts time the pairs)
   if (ref && opt.halo == 0) {

@@ -86,10 +86,12 @@ __device__ __noinline__ double slow_f2d(float v) { return (double)v; }
 __device__ __noinline__ float slow_d2f(double v) { return __double2float_rn(v); }
 
 // t / 4, exact: exponent decrement on the integer pipe, FP64 multiply only when
-// some lane of the warp needs it (zero, subnormal, inf/NaN).
-__device__ __forceinline__ double div_2d(double t) {
+// some live lane of the warp needs it (zero, subnormal, inf/NaN).  A lane that
+// holds no point (`live` false: its result is never stored) never calls for
+// the slow path: its t is typically 0.
+__device__ __forceinline__ double div_2d(double t, bool live = true) {
   const uint64_t b = f64_bits(t);
-  const bool fast = quarter_fast(b);
+  const bool fast = quarter_fast(b) || !live;
   double q = quarter_bits(b);
   if (!__all_sync(FULL_MASK, fast)) {
     if (!fast) q = slow_quarter(t);
@@ -98,10 +100,10 @@ __device__ __forceinline__ double div_2d(double t) {
 }
 
 // t / 6, correctly rounded, integer pipe (see exact_f64.cuh); IEEE division
-// only when some lane of the warp leaves the fast range.
-__device__ __forceinline__ double div_3d(double t) {
+// only when some live lane of the warp leaves the fast range.
+__device__ __forceinline__ double div_3d(double t, bool live = true) {
   const uint64_t b = f64_bits(t);
-  const bool fast = sixth_fast(b);
+  const bool fast = sixth_fast(b) || !live;
   double q = sixth_bits(b);
   if (!__all_sync(FULL_MASK, fast)) {
     if (!fast) q = slow_sixth(t);
@@ -110,9 +112,9 @@ __device__ __forceinline__ double div_3d(double t) {
 }
 
 template <int DIM>
-__device__ __forceinline__ double jdiv(double t) {
-  if constexpr (DIM == 2) return div_2d(t);
-  else return div_3d(t);
+__device__ __forceinline__ double jdiv(double t, bool live = true) {
+  if constexpr (DIM == 2) return div_2d(t, live);
+  else return div_3d(t, live);
 }
 
 template <int DIM>
@@ -638,8 +640,8 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
     if constexpr (WRITE) {
       double o0, o1;
       if constexpr (MODE == kModeSweep) {
-        o0 = jdiv<DIM>(t0);
-        o1 = jdiv<DIM>(t1);
+        o0 = jdiv<DIM>(t0, v0);
+        o1 = jdiv<DIM>(t1, v1);
       } else {
         o0 = c0;  // outer step: the updated iterate itself
         o1 = c1;
