@@ -72,11 +72,10 @@ FP64_ADDS_PER_LUP = {2: 3.0, 3: 5.0}
 BYTES_PER_LUP = {"f64": 24.0, "f32_refine": 12.0, "bf16_refine": 8.0}
 METRIC = "Jacobi GLUP/s & % HBM roofline, mixed vs FP64 at 1e-8 resid; p99 solve ms"
 # DRAM bytes (read + write) per lattice update of the 2D FP64 sweep kernel
-# (k_f64_march), from an ncu capture of one 4096^2 launch (270.2 MB read +
-# 106.0 MB written for 16.8 M updates); traffic grows with the points, so a
-# full launch is this times its points.  None once that kernel has changed
-# since the capture.
-F64_SWEEP_DRAM_BYTES_PER_LUP = (270.244608e6 + 106.030592e6) / (4096 * 4096)
+# (k_f64_march4, lines staged in shared memory), from an ncu capture of one
+# 8192^2 launch (1160.5 MB read + 506.9 MB written for 67.1 M updates).  None
+# once that kernel has changed since the capture.
+F64_SWEEP_DRAM_BYTES_PER_LUP = (1160.466e6 + 506.8544e6) / (8192 * 8192)
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -445,10 +444,11 @@ def run_ours(args, rank, world, local):
     if head == "f64":
         achieved = FP64_ADDS_PER_LUP[nd] * lup_rate / 1e9
         traffic = (F64_SWEEP_DRAM_BYTES_PER_LUP * p.points
-                   if (nd == 2 and args.emu <= 0 and args.march != 0 and F64_SWEEP_DRAM_BYTES_PER_LUP) else None)
+                   if (nd == 2 and args.emu <= 0 and args.march in (-1, 3) and F64_SWEEP_DRAM_BYTES_PER_LUP)
+                   else None)
         roof = {"bound": "alu", "kernel": "sweep_f64", "achieved": achieved, "peak": f64_peak,
                 "unit": "G FP64 adds/s", "frac": achieved / f64_peak, "traffic": traffic,
-                "traffic_note": "ncu dram read+write of a 4096^2 launch scaled by points" if traffic else None,
+                "traffic_note": "ncu dram read+write of one 8192^2 launch, per update times the points" if traffic else None,
                 "peak_kind": f64_peak_kind, "adds_per_lup": FP64_ADDS_PER_LUP[nd],
                 "nominal_frac": achieved / FP64_ADD_PEAK_NOMINAL_G,
                 "hbm": {"achieved": BYTES_PER_LUP[head] * lup_rate / 1e9, "peak": hbm_peak, "unit": "GB/s",
