@@ -460,11 +460,18 @@ __device__ __forceinline__ double dadd_int(double a, double b) {
 // (W + S) pair lane 0 would otherwise form, so lane 0 reads it from `rd`
 // (bit for bit the same value: addition is commutative) and the warp issues
 // one FP64 addition fewer per line.
+//
+// COLP (the block's first segment): the (W + S) pairs of the block's first
+// column, x[m][-1] + x[m-1][0], are formed kMarchLines lines at a time, one
+// line per lane, into the warp's shared buffer `colp`, and lane 0 reads them
+// there: one warp FP64 instruction per kMarchLines lines instead of one per
+// line (the same values: the same operands in the same order).
 template <int DIM, int MODE, bool PUSH, bool RESID, typename TE, typename TR, bool COH, int EMU = 0,
-          bool MARCH = false>
+          bool MARCH = false, bool COLP = false>
 __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __restrict__ blocks,
                                          const SolveDev* __restrict__ solves, int kpar, int epar,
-                                         const double* rd = nullptr, double* wr = nullptr, int pf = 0) {
+                                         const double* rd = nullptr, double* wr = nullptr, int pf = 0,
+                                         double* colp = nullptr) {
   constexpr bool WRITE = MODE != kModeResid && MODE != kModeOuterR;
   constexpr bool STORE_R = MODE == kModeOuter || MODE == kModeOuterR;
   const int lane = threadIdx.x & 31;
@@ -530,7 +537,8 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
     double sn0, sn1;
   };
   const bool has_eg = (lane == 31 && east_inner) || last1 || last0;
-  const bool has_wv = lane == 0 && !(MARCH && xs > 0);
+  constexpr bool COL = COLP && !MARCH && EMU < 3;  // first-column pairs from `colp`
+  const bool has_wv = lane == 0 && !(MARCH && xs > 0) && !(COL && xs == 0);
   auto fetch_aux = [&](int m, LineAux& a) {
     const int64_t lc = G.line(m);
     const int col = G.col(m);
@@ -583,6 +591,18 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
   double qacc = 0.0;  // residual: this lane's sum of r^2 over the current group
   double A0p = add(p1, c0);
   double A1p = add(pE, c1);
+  // first-column pairs of lines mc .. mc + kMarchLines - 1 (COL, first segment)
+  auto fill_col = [&](int mc) {
+    __syncwarp();
+    for (int j = lane; j < kMarchLines && mc + j < mend; j += 32) {
+      const int mm = mc + j;
+      colp[j] = add(src.one(gW + G.col(mm)), src.one(G.line(mm - 1)));
+    }
+    __syncwarp();
+  };
+  if constexpr (COL) {
+    if (xs == 0) fill_col(m0);
+  }
 
   for (int m = m0; m < mend; ++m) {
     const int64_t lc = G.line(m);
@@ -619,6 +639,13 @@ __device__ __forceinline__ void f64_item(const WorkItem& it, const BlockDev* __r
     } else if constexpr (EMU >= 3) {
       const double be = dadd_int(a.wv, p0);
       if (lane == 0) bw = be;
+    } else if constexpr (COL) {
+      if (xs == 0) {
+        if (m > m0 && ((m - m0) & (kMarchLines - 1)) == 0) fill_col(m);
+        if (lane == 0) bw = colp[(m - m0) & (kMarchLines - 1)];
+      } else if (lane == 0) {
+        bw = add(a.wv, p0);
+      }
     } else {
       if (lane == 0) bw = add(a.wv, p0);
     }
@@ -752,11 +779,13 @@ __global__ void __launch_bounds__(kThreads, DIM == 2 && (MODE == kModeSweep || M
                                             : (MODE == kModeOuter ? 2 : 1))
 k_f64(const WorkItem* __restrict__ items, int nitems, int kpar, const BlockDev* __restrict__ blocks,
       const SolveDev* __restrict__ solves, int epar) {
+  __shared__ double colp[kWarps][kMarchLines];
   const int w = blockIdx.x * kWarps + (threadIdx.x >> 5);
   if (w >= nitems) return;
   const WorkItem it = items[w];
   if (!solves[blocks[it.block].solve].active) return;
-  f64_item<DIM, MODE, PUSH, RESID, TE, TR, false, EMU>(it, blocks, solves, kpar, epar);
+  f64_item<DIM, MODE, PUSH, RESID, TE, TR, false, EMU, false, true>(it, blocks, solves, kpar, epar, nullptr, nullptr,
+                                                                   0, colp[threadIdx.x >> 5]);
 }
 
 // 2D FP64 sweep over march items: one warp per (block, range of lines),
