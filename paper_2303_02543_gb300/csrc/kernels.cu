@@ -1479,8 +1479,60 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
   const bool any = nvalid > 0;
   const int64_t gW = B.xoff;
   const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
-  PushTargets T;
-  if constexpr (PUSH) push_targets<DIM>(T, B, blocks, DIM == 2 ? y : (row_ok ? y : B.by - 1));
+  // halo push: the W / E ghost columns are kept by the lanes holding the
+  // block's first and last points; the march-axis faces and (3D) the side
+  // rows are looked up on the lines that write them
+  const int yrow = DIM == 2 ? y : (row_ok ? y : B.by - 1);
+  int64_t w_col = -1, e_col = -1;
+  if constexpr (PUSH) {
+    if (x == 0 && any && B.nbr[0] >= 0) {
+      const BlockDev& N = blocks[B.nbr[0]];
+      w_col = N.xoff + (int64_t)N.by * N.bz;  // the west neighbour's east ghost column
+    }
+    if (any && nvalid <= V && B.nbr[1] >= 0) e_col = blocks[B.nbr[1]].xoff;  // the east neighbour's west column
+  }
+  // the halo push of line m (values o of this lane's points)
+  auto push = [&](int m, int col, const float (&o)[V]) {
+    constexpr int lo = DIM == 2 ? 2 : 4;  // the march-axis faces
+    if (m == 0) {
+      const int nb = __ldg(&blocks[it.block].nbr[lo]);
+      if (nb >= 0) {
+        const Geo<DIM> GN(blocks[nb], yrow);
+        stv<V>(ed + GN.line(GN.extent) + x, o, nvalid);
+      }
+    }
+    if (m == G.extent - 1) {
+      const int nb = __ldg(&blocks[it.block].nbr[lo + 1]);
+      if (nb >= 0) {
+        const Geo<DIM> GN(blocks[nb], yrow);
+        stv<V>(ed + GN.line(-1) + x, o, nvalid);
+      }
+    }
+    if constexpr (DIM == 3) {
+      if (yrow == 0) {  // the S neighbour's north ghost row of plane m
+        const int nb = __ldg(&blocks[it.block].nbr[2]);
+        if (nb >= 0) {
+          const BlockDev& N = blocks[nb];
+          stv<V>(ed + N.off + (int64_t)(N.by + 1) * N.pitch + (int64_t)(m + 1) * N.plane + x, o, nvalid);
+        }
+      }
+      if (yrow == B.by - 1) {  // the N neighbour's south ghost row of plane m
+        const int nb = __ldg(&blocks[it.block].nbr[3]);
+        if (nb >= 0) {
+          const BlockDev& N = blocks[nb];
+          stv<V>(ed + N.off + (int64_t)(m + 1) * N.plane + x, o, nvalid);
+        }
+      }
+    }
+    if (w_col >= 0) ed[w_col + col] = from_f<TE>(o[0]);
+    if (e_col >= 0) {
+      float last = o[0];
+#pragma unroll
+      for (int k = 1; k < V; ++k)
+        if (k == nvalid - 1) last = o[k];
+      ed[e_col + col] = from_f<TE>(last);
+    }
+  };
 
   const int m0 = DIM == 2 ? it.y0 : it.z0;
   const int mend = m0 + it.n;
@@ -1544,20 +1596,7 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
       }
       if (any) {
         stv<V>(ed + lc + x, o, nvalid);
-        if constexpr (PUSH) {
-          if (m == 0 && T.lo_line >= 0) stv<V>(ed + T.lo_line + x, o, nvalid);
-          if (m == G.extent - 1 && T.hi_line >= 0) stv<V>(ed + T.hi_line + x, o, nvalid);
-          if (T.lo_side >= 0) stv<V>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
-          if (T.hi_side >= 0) stv<V>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
-          if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o[0]);
-          if (nvalid <= V && T.e_col >= 0) {
-            float last = o[0];
-#pragma unroll
-            for (int k = 1; k < V; ++k)
-              if (k == nvalid - 1) last = o[k];
-            ed[T.e_col + col] = from_f<TE>(last);
-          }
-        }
+        if constexpr (PUSH) push(m, col, o);
       }
       if (!more) break;
 #pragma unroll
@@ -1622,22 +1661,7 @@ __device__ __forceinline__ void low_item(const WorkItem& it, const BlockDev* __r
       }
       if (any) {
         stv<V>(ed + lc + x, o, nvalid);
-        if constexpr (PUSH) {
-          if (m == 0 && T.lo_line >= 0) stv<V>(ed + T.lo_line + x, o, nvalid);
-          if (m == G.extent - 1 && T.hi_line >= 0) stv<V>(ed + T.hi_line + x, o, nvalid);
-          if constexpr (DIM == 3) {
-            if (T.lo_side >= 0) stv<V>(ed + T.lo_side + (int64_t)(m + 1) * T.lo_side_step + x, o, nvalid);
-            if (T.hi_side >= 0) stv<V>(ed + T.hi_side + (int64_t)(m + 1) * T.hi_side_step + x, o, nvalid);
-          }
-          if (x == 0 && T.w_col >= 0) ed[T.w_col + col] = from_f<TE>(o[0]);
-          if (nvalid <= V && T.e_col >= 0) {
-            float last = o[0];
-#pragma unroll
-            for (int k = 1; k < V; ++k)
-              if (k == nvalid - 1) last = o[k];
-            ed[T.e_col + col] = from_f<TE>(last);
-          }
-        }
+        if constexpr (PUSH) push(m, col, o);
       }
       if constexpr (!FIRST) {
 #pragma unroll
