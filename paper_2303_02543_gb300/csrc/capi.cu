@@ -253,6 +253,7 @@ static int64_t* option_slot(Options& o, const char* key) {
   if (!strcmp(key, "autotune")) return &o.autotune;
   if (!strcmp(key, "emu_adds")) return &o.emu_adds;
   if (!strcmp(key, "tma")) return &o.tma;
+  if (!strcmp(key, "stage3")) return &o.stage3;
   if (!strcmp(key, "march")) return &o.march;
   if (!strcmp(key, "outer_split")) return &o.outer_split;
   if (!strcmp(key, "l2pf")) return &o.l2pf;
@@ -271,7 +272,7 @@ jacobi_status jacobi_set_option(jacobi_t ctx, const char* key, int64_t value) {
   if (k == "rows_low") require(value >= 0, "rows_low must be >= 0 (0: automatic)");
   if (k == "refine_period") require(value >= 1 && value <= 4096, "refine_period must be in [1, 4096]");
   if (k == "halo" || k == "profile" || k == "schedule" || k == "graph" || k == "poison_wait" || k == "autotune" ||
-      k == "tma" || k == "outer_split")
+      k == "tma" || k == "outer_split" || k == "stage3")
     require(value == 0 || value == 1, k + " must be 0 or 1");
   if (k == "march") require(value >= 0 && value <= 3, "march must be in [0, 3]");
   if (k == "l2pf") require(value >= 0 && value <= 64, "l2pf must be in [0, 64]");

@@ -887,6 +887,8 @@ void Workset::refine_inner(int64_t k) {
         LAUNCH(launch_sweep_low_tma(t, epar, push, low(), r_bf16_, cur_), "sweep low (staged)");
       else if (tma && j > 0)
         LAUNCH(launch_sweep_low_stage3(t, epar, push, low(), r_bf16_, estage_, cur_), "sweep low (staged, 3D)");
+      else if (ndim_ == 3 && opt.stage3 && j > 0)
+        LAUNCH(launch_sweep_low_s3(t, epar, push, low(), r_bf16_, cur_), "sweep low (lane-staged, 3D)");
       else LAUNCH(launch_sweep_low(t, epar, j == 0, push, low(), r_bf16_, cur_), "sweep low");
       prof_end(kProfSweepLow);
       if (!push) {

@@ -113,6 +113,7 @@ struct Options {
   int64_t autotune = 0;      // 1: pick rows/schedule by timing before the first solve
   int64_t emu_adds = 0;      // FP64 sweep: additions per warp step done on the integer pipe (0, 2, 3)
   int64_t tma = 0;           // inner sweeps (2D and 3D): stage lines in shared memory with bulk async copies
+  int64_t stage3 = 1;        // 3D inner sweeps after the first: each lane's lines staged ahead in shared memory
   int64_t march = 3;         // FP64 sweeps without a residual: one warp computes all segments of a line range
   int64_t outer_split = 1;   // 3D outer step as x += e over the layout, then the residual pass
   int64_t l2pf = 0;          // FP64 sweeps: lines ahead brought into L2 by bulk prefetches (0: none)

@@ -185,6 +185,9 @@ int launch_refine_outer_march(const Tables& t, int epar_last, bool push, int low
 // error or in 3D)
 int march_f64r_resident_warps(int ndim, bool push);
 int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, bool r_bf16, void* stream);
+// 3D inner sweep (not the first of a refinement step) with each lane's lines
+// staged ahead in shared memory by per-lane asynchronous copies (option stage3)
+int launch_sweep_low_s3(const Tables& t, int epar, bool push, int low, bool r_bf16, void* stream);
 // 2D inner sweep (not the first of a step) with rows staged in shared memory
 // by bulk asynchronous copies; a timed-out wait sets ctl->status bit 1.
 int launch_sweep_low_tma(const Tables& t, int epar, bool push, int low, bool r_bf16, void* stream);

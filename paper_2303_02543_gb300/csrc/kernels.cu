@@ -1698,6 +1698,198 @@ k_low_free(const WorkItem* __restrict__ items, int nitems, const BlockDev* __res
 }
 
 // ---------------------------------------------------------------------------
+// 3D inner sweep (not the first of a refinement step) with each lane's lines
+// staged ahead in shared memory.  For line m a lane needs, at its own V
+// points, e of line m + 1, e of the rows y - 1 and y + 1 on line m, and r of
+// line m.  It copies exactly those bytes with 16-byte asynchronous copies,
+// kLowS3Stages lines ahead, into its own slots of a per-warp ring, and reads
+// back only what it copied, so no barrier is needed, and the bytes in flight
+// hold no registers (the register form of low_item keeps one line ahead in
+// registers, which caps it at 2 CTAs per SM).  Items, arithmetic and halo
+// push are low_item's: bit-identical results.
+constexpr int kLowS3Stages = 4;
+
+// bytes of one line group of a warp: e of line m + 1, e of the rows y - 1 and
+// y + 1 (16 bytes per lane each), r (V values per lane)
+template <typename TE, typename TR>
+__host__ __device__ constexpr int low_s3_slot_bytes() {
+  return 32 * (3 * 16 + low_vpl<TE>() * (int)sizeof(TR));
+}
+
+template <bool PUSH, typename TE, typename TR>
+__global__ void __launch_bounds__(kThreads, sizeof(TE) == 4 ? 3 : 2)
+k_low_s3(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restrict__ blocks,
+         const SolveDev* __restrict__ solves, int epar) {
+  extern __shared__ __align__(16) unsigned char s3_smem[];
+  constexpr int V = low_vpl<TE>();
+  constexpr int RB = V * (int)sizeof(TR);  // bytes of r per lane and line
+  constexpr int SLOT = low_s3_slot_bytes<TE, TR>();
+  constexpr int NST = kLowS3Stages;
+  const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int w = blockIdx.x * kWarps + wi;
+  if (w >= nitems) return;
+  const WorkItem it = items[w];
+  const BlockDev B = blocks[it.block];
+  const SolveDev* S = solves + B.solve;
+  if (!S->active) return;
+  unsigned char* ring = s3_smem + wi * NST * SLOT;
+  const TE* __restrict__ es = reinterpret_cast<const TE*>(S->e[epar ^ 1]);
+  TE* __restrict__ ed = reinterpret_cast<TE*>(S->e[epar]);
+  const TR* __restrict__ rr = reinterpret_cast<const TR*>(S->r);
+
+  // a block row narrower than a warp row takes L = 2^lgL lanes and the warp
+  // computes 32 / L adjacent rows (as in low_item)
+  const int lgL = low_lanes_log2(B.bx, V);
+  const int L = 1 << lgL;
+  const int l = lane & (L - 1);
+  const int y = it.y0 + (lane >> lgL);
+  const bool row_ok = y < B.by;
+  const int yrow = row_ok ? y : B.by - 1;
+  const Geo<3> G(B, yrow);
+  const int bx = B.bx;
+  const int xs = it.seg * (L * V);
+  const int x = xs + V * l;
+  const int nvalid = row_ok ? bx - x : 0;  // > 0 when the lane holds points
+  const bool any = nvalid > 0;
+  const int64_t gW = B.xoff;
+  const int64_t gE = B.xoff + (int64_t)B.by * B.bz;
+  int64_t w_col = -1, e_col = -1;
+  if constexpr (PUSH) {
+    if (x == 0 && any && B.nbr[0] >= 0) {
+      const BlockDev& N = blocks[B.nbr[0]];
+      w_col = N.xoff + (int64_t)N.by * N.bz;  // the west neighbour's east ghost column
+    }
+    if (any && nvalid <= V && B.nbr[1] >= 0) e_col = blocks[B.nbr[1]].xoff;  // the east neighbour's west column
+  }
+  const int m0 = it.z0, mend = m0 + it.n;
+
+  auto slot = [&](int j) { return ring + ((unsigned)(j - m0) % (unsigned)NST) * SLOT; };
+  auto issue = [&](int j) {
+    if (j < mend && any) {
+      unsigned char* d = slot(j);
+      const int64_t lc = G.line(j);
+      cp_async_g2s<16>(d + lane * 16, es + G.line(j + 1) + x);
+      cp_async_g2s<16>(d + 512 + lane * 16, es + lc - G.side + x);
+      cp_async_g2s<16>(d + 1024 + lane * 16, es + lc + G.side + x);
+      cp_async_g2s<16>(d + 1536 + lane * RB, rr + lc + x);
+      if constexpr (RB == 32) cp_async_g2s<16>(d + 1536 + lane * RB + 16, rr + lc + x + 16 / (int)sizeof(TR));
+    }
+    cp_async_commit_group();
+  };
+  // the edge scalars of line m: west of point 0 (lane 0 of the row), east of
+  // point V - 1 (the row's last lane, when the row goes on), the east ghost
+  struct Edge {
+    float wv, ev, ge;
+  };
+  auto fetch_edge = [&](int m, Edge& q) {
+    q.wv = q.ev = q.ge = 0.f;
+    if (any) {
+      const int64_t lc = G.line(m);
+      const int col = G.col(m);
+      if (l == 0) q.wv = xs > 0 ? ldf<false>(es + lc + xs - 1) : ldf<false>(es + gW + col);
+      if (l == L - 1 && x + V < bx) q.ev = ldf<false>(es + lc + x + V);
+      if (nvalid <= V) q.ge = ldf<false>(es + gE + col);
+    }
+  };
+
+  float p[V], c[V];
+#pragma unroll
+  for (int k = 0; k < V; ++k) p[k] = c[k] = 0.f;
+  if (any) {
+    ldv<false, V>(es + G.line(m0 - 1) + x, p);
+    ldv<false, V>(es + G.line(m0) + x, c);
+  }
+#pragma unroll
+  for (int j = 0; j < NST; ++j) issue(m0 + j);
+  Edge cur;
+  fetch_edge(m0, cur);
+#pragma unroll 1
+  for (int m = m0; m < mend; ++m) {
+    const int64_t lc = G.line(m);
+    const int col = G.col(m);
+    const bool more = m + 1 < mend;
+    Edge nx;
+    nx.wv = nx.ev = nx.ge = 0.f;
+    if (more) fetch_edge(m + 1, nx);
+    cp_async_wait_group<NST - 1>();  // group m has landed
+    float n[V], sa[V], sb[V], rv[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) n[k] = sa[k] = sb[k] = rv[k] = 0.f;
+    if (any) {
+      const unsigned char* d = slot(m);
+      unpack_smem<V>(reinterpret_cast<const TE*>(d + lane * 16), n);
+      unpack_smem<V>(reinterpret_cast<const TE*>(d + 512 + lane * 16), sa);
+      unpack_smem<V>(reinterpret_cast<const TE*>(d + 1024 + lane * 16), sb);
+      unpack_smem<V>(reinterpret_cast<const TR*>(d + 1536 + lane * RB), rv);
+    }
+    issue(m + NST);  // group m + NST into the slot group m leaves
+    float wv = __shfl_up_sync(FULL_MASK, c[V - 1], 1, L);
+    if (l == 0) wv = cur.wv;
+    float ev = __shfl_down_sync(FULL_MASK, c[0], 1, L);
+    if (l == L - 1 && x + V < bx) ev = cur.ev;
+    float o[V];
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      const float west = k == 0 ? wv : c[k - 1];
+      float east = k == V - 1 ? ev : c[k + 1];
+      if (k + 1 == nvalid) east = cur.ge;  // the block's last point takes the ghost
+      float t = __fadd_rn(__fadd_rn(west, p[k]), __fadd_rn(east, n[k]));
+      t = __fadd_rn(t, __fadd_rn(sa[k], sb[k]));
+      t = __fadd_rn(t, rv[k]);
+      o[k] = jdivf<3>(t);
+    }
+    if (any) {
+      stv<V>(ed + lc + x, o, nvalid);
+      if constexpr (PUSH) {
+        if (m == 0) {  // the D neighbour's upper ghost plane
+          const int nb = __ldg(&blocks[it.block].nbr[4]);
+          if (nb >= 0) {
+            const Geo<3> GN(blocks[nb], yrow);
+            stv<V>(ed + GN.line(GN.extent) + x, o, nvalid);
+          }
+        }
+        if (m == G.extent - 1) {  // the U neighbour's lower ghost plane
+          const int nb = __ldg(&blocks[it.block].nbr[5]);
+          if (nb >= 0) {
+            const Geo<3> GN(blocks[nb], yrow);
+            stv<V>(ed + GN.line(-1) + x, o, nvalid);
+          }
+        }
+        if (yrow == 0) {  // the S neighbour's north ghost row of plane m
+          const int nb = __ldg(&blocks[it.block].nbr[2]);
+          if (nb >= 0) {
+            const BlockDev& N = blocks[nb];
+            stv<V>(ed + N.off + (int64_t)(N.by + 1) * N.pitch + (int64_t)(m + 1) * N.plane + x, o, nvalid);
+          }
+        }
+        if (yrow == B.by - 1) {  // the N neighbour's south ghost row of plane m
+          const int nb = __ldg(&blocks[it.block].nbr[3]);
+          if (nb >= 0) {
+            const BlockDev& N = blocks[nb];
+            stv<V>(ed + N.off + (int64_t)(m + 1) * N.plane + x, o, nvalid);
+          }
+        }
+        if (w_col >= 0) ed[w_col + col] = from_f<TE>(o[0]);
+        if (e_col >= 0) {
+          float last = o[0];
+#pragma unroll
+          for (int k = 1; k < V; ++k)
+            if (k == nvalid - 1) last = o[k];
+          ed[e_col + col] = from_f<TE>(last);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+      p[k] = c[k];
+      c[k] = n[k];
+    }
+    cur = nx;
+  }
+  cp_async_wait_group<0>();  // nothing may still target this warp's ring
+}
+
+// ---------------------------------------------------------------------------
 // Two inner sweeps in one pass (temporal blocking, 2D): e2 = J(J(e0)) with
 // J(e)_p = (((W + S) + (E + N)) + r_p) / 4, the arithmetic of low_item.  The
 // intermediate e1 never leaves shared memory and is rounded to the storage
@@ -3258,6 +3450,25 @@ int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, 
   cudaStream_t s = (cudaStream_t)stream;
   return t.ndim == 2 ? low_dim<2>(t, epar, first, push, low, r_bf16, s)
                      : low_dim<3>(t, epar, first, push, low, r_bf16, s);
+}
+
+template <typename TE, typename TR>
+static int low_s3_typed(const Tables& t, int epar, bool push, cudaStream_t s) {
+  if (t.nlo == 0) return 0;
+  constexpr int sm = kWarps * kLowS3Stages * low_s3_slot_bytes<TE, TR>();
+  auto k = push ? k_low_s3<true, TE, TR> : k_low_s3<false, TE, TR>;
+  const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  if (e != cudaSuccess) return (int)e;
+  k<<<grid_of(t.nlo, kWarps), kThreads, sm, s>>>(t.wlo, t.nlo, t.blocks, t.solves, epar);
+  return (int)cudaGetLastError();
+}
+
+int launch_sweep_low_s3(const Tables& t, int epar, bool push, int low, bool r_bf16, void* stream) {
+  cudaStream_t s = (cudaStream_t)stream;
+  if (t.ndim != 3) return (int)cudaErrorInvalidValue;
+  if (low == kLowF32) return low_s3_typed<float, float>(t, epar, push, s);
+  if (r_bf16) return low_s3_typed<__nv_bfloat16, __nv_bfloat16>(t, epar, push, s);
+  return low_s3_typed<__nv_bfloat16, float>(t, epar, push, s);
 }
 
 template <int DIM, typename TE, typename TR>

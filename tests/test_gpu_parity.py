@@ -429,6 +429,33 @@ def test_march_outer_step_bit_exact(dtype, e16, r16, halo, dims, block, period):
     assert np.array_equal(res[3][3], x_o)
 
 
+@pytest.mark.parametrize("dtype,e16,r16", [("f32_refine", False, False), ("bf16_refine", True, False),
+                                           ("bf16r16_refine", True, True)])
+@pytest.mark.parametrize("halo", [0, 1])
+@pytest.mark.parametrize("dims,block,period", [((40, 33, 20), (32, 11, 20), 20), ((70, 9, 8), (64, 5, 4), 7),
+                                               ((16, 14, 12), (8, 7, 6), 10), ((130, 20, 9), (64, 16, 9), 6),
+                                               ((5, 6, 7), (1, 1, 1), 5), ((200, 12, 10), (200, 12, 10), 9)])
+def test_lane_staged_3d_inner_sweeps_bit_exact(dtype, e16, r16, halo, dims, block, period):
+    """3D inner sweeps with each lane's e and r values staged four lines ahead
+    in shared memory (stage3 = 1, the default) against one line ahead in
+    registers (stage3 = 0) and the oracle's emulation: the same status, sweep
+    count and field bits, over rows narrower than a warp, 1-point blocks,
+    remainders, both halo modes and all three storage types."""
+    p = inputs.make_problem(dims, block, 63, boundary="uniform", source="normal", x0="zero")
+    res = {}
+    for st3 in (0, 1):
+        with solver(p, dtype=dtype, refine_period=period, stage3=st3, halo=halo) as s:
+            st, sw, rel = s.solve(1e-8, 10 ** 6)
+            res[st3] = (st, sw, rel, s.field())
+    assert res[1][:3] == res[0][:3]
+    assert np.array_equal(res[1][3], res[0][3])
+    st_o, x_o, sw_o, _ = oracle.refine_solve(p.dims, p.faces, p.source, None, 1e-8, 10 ** 6, period,
+                                             e_bf16=e16, r_bf16=r16)
+    assert res[1][0] == J.OK and st_o == oracle.OK
+    assert res[1][1] == sw_o
+    assert np.array_equal(res[1][3], x_o)
+
+
 def test_residual_decomposition_independent_3d():
     p = inputs.make_problem((130, 20, 40), (130, 20, 40), 58, boundary="uniform", source="normal", x0="uniform")
     vals = []
