@@ -193,10 +193,11 @@ jacobi_status jacobi_set_source(jacobi_t ctx, const double* in, int on_device);
  *                    copies (2D: the warp's line of e and r; 3D: its rows of
  *                    e with the rows above and below, and of r)
  *   "stage3"         1 (default): 3D inner sweeps after the first of a
- *                    refinement step stage, per lane and four lines ahead, the
- *                    e and r values each lane reads, in shared memory by
- *                    16-byte async copies that each lane reads back itself;
- *                    0: one line ahead in registers (bit-identical)
+ *                    refinement step stage the e and r values each lane
+ *                    reads, three (float) or four (bfloat16) lines ahead, in
+ *                    shared memory by 16-byte async copies that each lane
+ *                    reads back itself; 0: one line ahead in registers
+ *                    (bit-identical)
  *   "tb"             2: in 2D, with the fused halo and one launch per sweep,
  *                    the inner sweeps run two per launch (temporal blocking:
  *                    one CTA per tile of 32 x 128 points keeps the first

@@ -1702,12 +1702,17 @@ k_low_free(const WorkItem* __restrict__ items, int nitems, const BlockDev* __res
 // staged ahead in shared memory.  For line m a lane needs, at its own V
 // points, e of line m + 1, e of the rows y - 1 and y + 1 on line m, and r of
 // line m.  It copies exactly those bytes with 16-byte asynchronous copies,
-// kLowS3Stages lines ahead, into its own slots of a per-warp ring, and reads
+// low_s3_stages lines ahead, into its own slots of a per-warp ring, and reads
 // back only what it copied, so no barrier is needed, and the bytes in flight
 // hold no registers (the register form of low_item keeps one line ahead in
 // registers, which caps it at 2 CTAs per SM).  Items, arithmetic and halo
 // push are low_item's: bit-identical results.
-constexpr int kLowS3Stages = 4;
+// lines staged ahead (measured at 512^3: float 305.7 us per sweep with 3,
+// 350.8 with 4, 382.5 with 6; bfloat16 351.4 with 3, 342.5 with 4)
+template <typename TE>
+__host__ __device__ constexpr int low_s3_stages() {
+  return sizeof(TE) == 4 ? 3 : 4;
+}
 
 // bytes of one line group of a warp: e of line m + 1, e of the rows y - 1 and
 // y + 1 (16 bytes per lane each), r (V values per lane)
@@ -1724,7 +1729,7 @@ k_low_s3(const WorkItem* __restrict__ items, int nitems, const BlockDev* __restr
   constexpr int V = low_vpl<TE>();
   constexpr int RB = V * (int)sizeof(TR);  // bytes of r per lane and line
   constexpr int SLOT = low_s3_slot_bytes<TE, TR>();
-  constexpr int NST = kLowS3Stages;
+  constexpr int NST = low_s3_stages<TE>();
   const int wi = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int w = blockIdx.x * kWarps + wi;
   if (w >= nitems) return;
@@ -3455,7 +3460,7 @@ int launch_sweep_low(const Tables& t, int epar, bool first, bool push, int low, 
 template <typename TE, typename TR>
 static int low_s3_typed(const Tables& t, int epar, bool push, cudaStream_t s) {
   if (t.nlo == 0) return 0;
-  constexpr int sm = kWarps * kLowS3Stages * low_s3_slot_bytes<TE, TR>();
+  constexpr int sm = kWarps * low_s3_stages<TE>() * low_s3_slot_bytes<TE, TR>();
   auto k = push ? k_low_s3<true, TE, TR> : k_low_s3<false, TE, TR>;
   const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
   if (e != cudaSuccess) return (int)e;
