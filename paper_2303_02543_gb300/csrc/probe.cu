@@ -3,9 +3,10 @@
 // The plain FP64 Jacobi sweep is bound by its FP64 additions on GB300, not by
 // HBM (the FP64 pipe runs at a small fraction of the FP32 rate), so its
 // roofline is the FP64 pipe's measured throughput.  Every FP64 addition of
-// the sweep kernels is issued as fma.rn.f64 d, a, 1.0, b; this probe times
-// that same instruction form in `chains` independent dependency chains per
-// thread, with `ctas_per_sm` CTAs of 256 threads resident per SM.  With
+// the sweep kernels is issued as fma.rn.f64 d, a, one, b with `one` = 1.0 in
+// a register (form 1 below, the fastest form on GB300); this probe times that
+// instruction form and the others in `chains` independent dependency chains
+// per thread, with `ctas_per_sm` CTAs of 256 threads resident per SM.  With
 // enough independent chains the rate is the pipe's throughput; with one chain
 // it shows the dependent-issue latency that the sweeps must hide.
 #include <cuda_runtime.h>

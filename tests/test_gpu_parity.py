@@ -259,6 +259,12 @@ def test_invalid_arguments():
             s.set_option("check_every", 0)
         with pytest.raises(J.JacobiError):
             s.set_option("no_such_option", 1)
+        # the defaults of the measured forms, and their ranges
+        assert s.get_option("march") == 3 and s.get_option("stage3") == 1
+        for key, bad in (("march", 4), ("stage3", 2), ("tb", 3), ("march", -1)):
+            with pytest.raises(J.JacobiError):
+                s.set_option(key, bad)
+        assert s.get_option("march") == 3
         st = J.load().jacobi_solve(s.h, -1.0, 10, None, None)
         assert st == J.ERR_INVALID
         s.sweep(0)
