@@ -1,6 +1,7 @@
 // Host engine of the GB300 Jacobi library: block layout, work tables, launch
 // sequences, solve loops, CUDA graphs and the autotuner.  See engine.h.
 #include "engine.h"
+#include "deal_runs.h"
 
 #include <algorithm>
 #include <chrono>
@@ -441,38 +442,20 @@ void Workset::rebuild_tables() {
     }
   }
   // option march 3: the lines of all blocks, in block order, dealt out in
-  // equal runs, one per warp (as many warps as the kernel keeps resident, but
-  // runs of at least 8 lines, and more warps only where a run would exceed
-  // kMarchLines); a run crossing a block boundary becomes two items.  `unit` lines per step: 1 for the plain
-  // sweep, kResGroup for the fused-residual sweep and the outer step, whose
-  // items must hold whole residual groups.
+  // equal runs, one per warp (deal_runs.h: as many warps as the kernel keeps
+  // resident, but runs of at least 8 lines, and more warps only where a run
+  // would exceed kMarchLines); a run crossing a block boundary becomes two
+  // items.  `unit` lines per step: 1 for the plain sweep, kResGroup for the
+  // fused-residual sweep and the outer step, whose items must hold whole
+  // residual groups.
   std::vector<int> wms, wmrs;
   auto deal = [&](int64_t target, int unit, std::vector<WorkItem>& out, std::vector<int>& start) {
-    int64_t total = 0;
-    for (const auto& mb : mblk) total += (mb.second + unit - 1) / unit;
-    if (total == 0) return;
-    const int64_t wmax = kMarchLines / unit, wmin = std::max(1, 8 / unit);  // runs of 8 to kMarchLines lines
-    const int64_t nw = std::max<int64_t>(std::min<int64_t>(std::max<int64_t>(target, 1), (total + wmin - 1) / wmin),
-                                         (total + wmax - 1) / wmax);
-    size_t bk = 0;
-    int64_t used = 0;  // units of block mblk[bk] already dealt
-    for (int64_t w = 0; w < nw; ++w) {
-      start.push_back((int)out.size());
-      int64_t need = (w + 1) * total / nw - w * total / nw;
-      while (need > 0 && bk < mblk.size()) {
-        const int64_t units = (mblk[bk].second + unit - 1) / unit;
-        const int64_t take = std::min(need, units - used);
-        const int a = (int)(used * unit), e = (int)std::min<int64_t>((used + take) * unit, mblk[bk].second);
-        out.push_back(WorkItem{mblk[bk].first, 0, (int16_t)(e - a), a, 0});
-        used += take;
-        need -= take;
-        if (used == units) {
-          ++bk;
-          used = 0;
-        }
-      }
-    }
-    start.push_back((int)out.size());
+    std::vector<RunPiece> pieces;
+    std::vector<int> st;
+    deal_runs(mblk, target, unit, 8, kMarchLines, pieces, st);
+    const int base = (int)out.size();
+    for (const RunPiece& q : pieces) out.push_back(WorkItem{q.block, 0, (int16_t)q.n, q.y0, 0});
+    for (int v : st) start.push_back(base + v);
   };
   if (!mblk.empty()) {
     deal(march_f64_resident_warps(ndim_, opt.halo == 0, march_width(3)), 1, wm, wms);

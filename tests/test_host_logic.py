@@ -79,6 +79,21 @@ def test_serving_arena_first_fit_matches_brute_force(tmp_path):
     assert "failures 0" in r.stdout
 
 
+def test_march_runs_dealt_to_warps_meet_their_contract(tmp_path):
+    """The dealing of block lines to warps in equal runs (deal_runs.h,
+    host-only C++; the 2D FP64 march items) on random block lists: every line
+    covered once in block order, pieces inside one block on step boundaries,
+    the stated warp count, runs equal to within one step and never longer than
+    a warp's shared pair buffer."""
+    src = os.path.join(ROOT, "tests", "native", "deal_runs_check.cpp")
+    exe = str(tmp_path / "deal_runs_check")
+    subprocess.run(["g++", "-O2", "-std=c++17", "-Wall", "-Wextra", "-Werror",
+                    "-I", os.path.join(ROOT, "paper_2303_02543_gb300", "csrc"), "-o", exe, src], check=True)
+    r = subprocess.run([exe, "20000"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "failures 0" in r.stdout
+
+
 def test_torch_allocator_trampolines_are_created_once():
     """A context keeps the allocator hooks it was created with; reinstalling
     must not free the ctypes trampolines those hooks point to."""
