@@ -6,6 +6,7 @@ import os
 import re
 import subprocess
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -92,6 +93,31 @@ def test_march_runs_dealt_to_warps_meet_their_contract(tmp_path):
     r = subprocess.run([exe, "20000"], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "failures 0" in r.stdout
+
+
+def test_one_rounding_residual_equals_the_oracles_subtraction():
+    """The kernels form the 2D residual t - 4x as one fused multiply-add,
+    RN(t - 4x); the oracle subtracts the product, RN(t - RN(4x)).  4x is exact
+    wherever it is finite, so the two agree: checked here on random doubles of
+    every magnitude, with the exact difference rounded once (Fraction -> float
+    rounds to nearest-even), against the double arithmetic of the oracle."""
+    from fractions import Fraction
+    rng = np.random.default_rng(2312)
+    for _ in range(20000):
+        x = float(rng.standard_normal() * 2.0 ** int(rng.integers(-300, 300)))
+        t = float(rng.standard_normal() * 2.0 ** int(rng.integers(-300, 300)))
+        if rng.random() < 0.3:
+            t = 4.0 * x * (1.0 + float(rng.standard_normal()) * 2.0 ** -int(rng.integers(1, 60)))  # cancellation
+        one_rounding = float(Fraction(t) - 4 * Fraction(x))
+        assert one_rounding == t - 4.0 * x
+    # with 6 (3D) the product is not exact and one rounding differs from two,
+    # which is why the 3D kernels round 6x first and then fma(6x, -1, t)
+    diff = 0
+    for _ in range(20000):
+        x = float(rng.standard_normal())
+        t = 6.0 * x * (1.0 + float(rng.standard_normal()) * 2.0 ** -int(rng.integers(1, 40)))
+        diff += float(Fraction(t) - 6 * Fraction(x)) != t - 6.0 * x
+    assert diff > 0
 
 
 def test_torch_allocator_trampolines_are_created_once():
