@@ -43,3 +43,46 @@ def test_cpu_baseline_leg_reports_all_cores_and_one_thread():
     assert cb["kind"] == "oracle" and cb["unit"] == "GLUP/s" and cb["value"] > 0 and cb["cores"] >= 1
     st = cb["single_thread"]
     assert st["cores"] == 1 and st["value"] > 0
+
+
+def test_serving_leg_counts_censored_requests_in_the_all_request_bound(monkeypatch):
+    """The serving leg's host logic against a fake server: completed requests
+    give p50/p99 over their latencies; requests still running at the deadline
+    are censored and enter the all-request percentiles with their waiting
+    time so far (a lower bound)."""
+    import types
+    sys.path.insert(0, ROOT)
+    import bench
+    from paper_2303_02543_gb300 import inputs
+    from paper_2303_02543_gb300 import jacobi as J
+
+    arrivals = [types.SimpleNamespace(t=0.0, problem=types.SimpleNamespace(points=100)) for _ in range(4)]
+    monkeypatch.setattr(inputs, "serving_stream", lambda **kw: arrivals)
+
+    class FakeServer:
+        def __init__(self, *a, **kw):
+            self.n = 0
+
+        def submit(self, problem, tol, max_sweeps):
+            self.n += 1
+            return self.n
+
+        def stats(self):
+            return {"completed": 2, "rejected": 0, "steps": 7, "evictions": 0, "resumed": 0}
+
+        def poll(self, ticket, want_field=True):
+            # tickets 1 and 2 finished in 0.1 s and 0.3 s; 3 and 4 still run
+            return (J.OK, 10, 1e-9, 0.1 * (2 * ticket - 1), None) if ticket <= 2 else None
+
+        def close(self):
+            pass
+
+    monkeypatch.setattr(J, "Server", FakeServer)
+    import torch
+    monkeypatch.setattr(torch.cuda, "set_device", lambda d: None)
+    leg = bench.serving_leg(1.0, 0.0, 256, 64, 0, grace=0.05)
+    assert leg["requests"] == 4 and leg["completed"] == 2 and leg["censored"] == 2
+    assert abs(leg["p50_ms"] - 300.0) < 1e-6 and abs(leg["p99_ms"] - 300.0) < 1e-6
+    # the censored requests have waited at least the grace period
+    assert leg["p99_ms_all_lower_bound"] >= 50.0 and leg["p50_ms_all_lower_bound"] >= 100.0
+    assert leg["glups"] > 0 and leg["steps"] == 7
